@@ -1,0 +1,419 @@
+#!/usr/bin/env python3
+"""STKDE benchmark: voxel-point updates/s and ms per grid on GB300.
+
+One step = one stkde_compute of the whole hot path (re-centre, binning sort,
+bin bounds + gather, tile kernel writing every voxel) on a synthetic clustered
+event set already resident in HBM.  Default workload: n = 2,000,000 events,
+1024 x 1024 x 512 grid, hs = 25, ht = 20 voxels (the large configuration), in
+the tensor bf16x3 form.  The L2 is flushed (256 MiB write) before every timed
+step; the 2.1 GB output is also larger than L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank computes its own instance (seed offset = rank): the
+instances are independent, so scaling is weak and no collective touches the
+data; the only collectives are the barrier and the max-over-ranks of the time.
+``--impl reference`` times the FP64 CPU oracle (the paper has no GPU code) on a
+bounded sample of tiles of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1705_09366_gb300 import synth  # noqa: E402
+
+METRIC = "STKDE voxel-updates/s & ms/grid vs plain GPU at stated err; serve p50/p99"
+UNIT = "voxel-point updates/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+ERR_GATE = {"bf16x3": 2e-5, "fp16x3": 1e-5, "fp32": 1e-5, "scatter": 1e-5}
+PRODUCTS = {"bf16x3": 3, "fp16x3": 3, "fp32": 1, "scatter": 1}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(synth.WORKLOADS), default="large")
+    ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "fp16x3", "fp32", "scatter"])
+    ap.add_argument("--compare", default="fp32,scatter",
+                    help="other forms timed beside the main one ('' for none)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+# ----------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for ln in f:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        loaded = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------ CPU oracle ---
+
+def tile_boxes(w, seed=0):
+    """All 16 x 8 x gt tile boxes of the grid in a seeded random order."""
+    nx, ny = (w.gx + 15) // 16, (w.gy + 7) // 8
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(nx * ny)
+    return [(int(c // ny) * 16, min(w.gx, int(c // ny) * 16 + 16), int(c % ny) * 8,
+             min(w.gy, int(c % ny) * 8 + 8), 0, w.gt) for c in order]
+
+
+def oracle_sample(w, seconds, seed=0, calib=None):
+    """Times the FP64 oracle (Algorithm 2 on sampled tiles, all host cores) for
+    about `seconds`; returns (pairs, elapsed, boxes, results)."""
+    import oracle
+    p = oracle.params(w.gx, w.gy, w.gt, w.hs, w.ht, x0=w.x0, y0=w.y0, t0=w.t0, sres=w.sres,
+                      tres=w.tres)
+    boxes = tile_boxes(w, seed)
+    if calib is None:
+        t = time.perf_counter()
+        _, c = oracle.pb_boxes(w.points, p, boxes[:4], with_slack=False, pair_counts=True)
+        dt = max(time.perf_counter() - t, 1e-3)
+        per_box = dt / 4
+    else:
+        per_box = calib
+    k = int(max(1, min(len(boxes), round(seconds / per_box))))
+    sel = boxes[:k]
+    t = time.perf_counter()
+    res, counts = oracle.pb_boxes(w.points, p, sel, with_slack=True, pair_counts=True)
+    dt = time.perf_counter() - t
+    return int(counts.sum()), dt, sel, res, dt / k
+
+
+# ------------------------------------------------------------- reference ---
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w = synth.WORKLOADS[args.workload]()
+    total_budget = 150.0
+    per_step = max(1.0, total_budget / max(1, args.steps + args.warmup))
+    _, _, _, _, per_box = oracle_sample(w, 0.5)
+    vals = []
+    ntiles = []
+    for i in range(args.warmup + args.steps):
+        pairs, dt, sel, _, _ = oracle_sample(w, per_step, seed=i, calib=per_box)
+        if i >= args.warmup:
+            vals.append((pairs, dt))
+            ntiles.append(len(sel))
+    pairs = sum(v[0] for v in vals)
+    secs = sum(v[1] for v in vals)
+    value = pairs / secs
+    cores = oracle.max_threads()
+    tiles = int(round(statistics.mean(ntiles)))
+    sample = (f"FP64 oracle (Algorithm 2) on {tiles} random 16x8x{w.gt} tiles per step of the "
+              f"{w.name} workload, {cores} host threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / len(vals),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "grid": [w.gx, w.gy, w.gt], "hs": w.hs,
+                   "ht": w.ht, "sample": "tiles"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- ours ---
+
+def run_ours(args):
+    import torch
+    import paper_1705_09366_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    peaks, peaks_src = load_peaks()
+    w = synth.WORKLOADS[args.workload](seed_offset=rank)
+    dims = (w.gx, w.gy, w.gt)
+    stream = torch.cuda.current_stream(dev)
+    pts = torch.from_numpy(w.points).to(dev)
+    out = torch.empty(dims, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    ctx = pkg.Context(device=local, stream=stream, form=args.form, profile=False)
+    updates = ctx.count_updates(pts, dims, w.hs, w.ht)
+
+    # ---- timed steps: device-resident inputs, L2 flushed before each step
+    for _ in range(args.warmup):
+        ctx.compute(pts, dims, w.hs, w.ht, out=out)
+    ctx.synchronize()
+    launches_per_step = ctx.last_launch_count()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    barrier()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        ctx.compute(pts, dims, w.hs, w.ht, out=out)
+        ends[i].record(stream)
+    barrier()
+    clk = clocks.stop() if rank == 0 else None
+    ctx.synchronize()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = max_over_ranks(sum(step_ms) / 1000.0)
+    all_updates = sum_over_ranks(float(updates) * args.steps)
+    value = all_updates / total_s
+    ms_per_step = 1000.0 * total_s / args.steps
+
+    # ---- dominant kernel: library events around each phase (same stream)
+    pctx = pkg.Context(device=local, stream=stream, form=args.form, profile=True)
+    phases = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        pctx.compute(pts, dims, w.hs, w.ht, out=out)
+        phases.append(pctx.phase_times())
+    pctx.synchronize()
+    pctx.close()
+    ph = np.array(phases)
+    phase_ms = {name: float(ph[:, k].mean()) for k, name in
+                enumerate(["recentre", "sort", "bounds_gather", "tile"][:ph.shape[1]])}
+    tile_ms = phase_ms.get("tile", float("nan"))
+
+    grid_bytes = 4 * w.gx * w.gy * w.gt
+    prods = PRODUCTS[args.form]
+    flops = 2.0 * prods * updates
+    if args.form in ("bf16x3", "fp16x3"):
+        peak = peaks["bf16_tflops"]
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "achieved": flops / (tile_ms * 1e-3) / 1e12, "peak": peak}
+        roof["frac"] = roof["achieved"] / peak
+        roof["note"] = (f"algorithmic FLOPs = 2 x {prods} products x {updates} voxel-point "
+                        f"updates; peak = {peaks_src} dense bf16 (burst)")
+    else:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = 2.0 * 128 * sms * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s",
+                "achieved": flops / (tile_ms * 1e-3) / 1e12, "peak": peak}
+        roof["frac"] = roof["achieved"] / peak
+        roof["note"] = f"peak = {sms} SMs x 128 FP32 lanes x 2 x max SM clock"
+    hbm = grid_bytes / (tile_ms * 1e-3) / 1e9
+    roof["hbm_write_gbs"] = hbm
+    roof["hbm_frac_of_" + peaks_src] = hbm / peaks["hbm_gbs"]
+    roof["traffic"] = None
+    roof["kernel_ms"] = tile_ms
+    roof["roofline_ms"] = 1e3 * max(grid_bytes / (peaks["hbm_gbs"] * 1e9),
+                                    (flops / (peak * 1e12)))
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if args.e2e_steps > 0:
+        hpts = torch.from_numpy(w.points).pin_memory()
+        hout = torch.empty(dims, dtype=torch.float32, pin_memory=True)
+        ctx.compute(hpts, dims, w.hs, w.ht, out=hout)
+        ctx.synchronize()
+        barrier()
+        t = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.compute(hpts, dims, w.hs, w.ht, out=hout)
+            ctx.synchronize()
+        barrier()
+        e2e_s = max_over_ranks(time.perf_counter() - t)
+        e2e = {"value": sum_over_ranks(float(updates) * args.e2e_steps) / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(w.points.nbytes), "d2h_bytes_per_step": grid_bytes,
+               "ms_per_step": 1e3 * e2e_s / args.e2e_steps}
+        del hout, hpts
+
+    # ---- other forms on the same input (rank 0, N = 1)
+    forms = {args.form: {"ms_per_grid": ms_per_step, "updates_per_s": value / max(world, 1),
+                         "tile_kernel_ms": tile_ms}}
+    if rank == 0 and world == 1 and args.compare:
+        for f in [x for x in args.compare.split(",") if x and x != args.form]:
+            fo = torch.empty(dims, dtype=torch.float32, device=dev)
+            with pkg.Context(device=local, stream=stream, form=f) as fc:
+                reps = 1 if f == "scatter" else 3
+                fc.compute(pts, dims, w.hs, w.ht, out=fo)
+                fc.synchronize()
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                tot = 0.0
+                for i in range(reps):
+                    flush.fill_(float(i))
+                    s0.record(stream)
+                    fc.compute(pts, dims, w.hs, w.ht, out=fo)
+                    s1.record(stream)
+                    fc.synchronize()
+                    tot += s0.elapsed_time(s1)
+                forms[f] = {"ms_per_grid": tot / reps, "updates_per_s": updates / (tot / reps * 1e-3)}
+            forms[f]["_out"] = fo
+
+    # ---- CPU oracle baseline + error against it on the sampled tiles (rank 0, N = 1)
+    cpu = None
+    errs = {}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        pairs, dt, boxes, res, _ = oracle_sample(w, args.cpu_seconds, seed=rank)
+        cores = oracle.max_threads()
+        cpu = {"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle (Algorithm 2) on {len(boxes)} random 16x8x{w.gt} tiles "
+                         f"of the {w.name} workload ({pairs} updates, {dt:.1f} s)"}
+        scale = max(r.max() for r, _ in res)
+        for f, buf in [(args.form, out)] + [(k, v["_out"]) for k, v in forms.items() if "_out" in v]:
+            worst = 0.0
+            for (x0, x1, y0, y1, t0, t1), (ref, slack) in zip(boxes, res):
+                got = buf[x0:x1, y0:y1, t0:t1].double().cpu().numpy()
+                ex = np.maximum(np.abs(got - ref) - slack, 0.0).max()
+                worst = max(worst, float(ex / scale))
+            errs[f] = worst
+            forms[f]["max_rel_err"] = worst
+            forms[f]["err_gate"] = ERR_GATE[f]
+    for v in forms.values():
+        v.pop("_out", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16x3": "bf16", "fp16x3": "f16", "fp32": "f32", "scatter": "f32"}[args.form],
+            "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "grid": [w.gx, w.gy, w.gt], "hs": w.hs,
+                       "ht": w.ht, "form": args.form, "updates_per_grid": updates,
+                       "l2": "flushed before each step (256 MiB write); output 2.1 GB > L2",
+                       "parallelism": f"{world} independent instance(s), one per GPU"},
+            "roofline": roof,
+            "phase_ms": phase_ms,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "forms": forms,
+            "max_rel_err": errs.get(args.form),
+            "peaks": peaks_src,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,168 @@
+/*
+ * stkde.h -- C ABI of the GB300 space-time kernel density estimation library.
+ *
+ * The library computes the STKDE density of Section 2.1 (the density equation
+ * with kernels k_s and k_t) on a voxel grid:
+ *
+ *   out[X][Y][T] = 1/(n hs^2 ht) * sum_i [d_i < hs] [|t - t_i| <= ht]
+ *                  k_s((x - x_i)/hs, (y - y_i)/hs) * k_t((t - t_i)/ht)
+ *
+ * sampled at voxel centres x = x0 + (X + 1/2) sres, y = y0 + (Y + 1/2) sres,
+ * t = t0 + (T + 1/2) tres, with k_s(u,v) = c_s (1-u^2)(1-v^2) and
+ * k_t(w) = c_t (1-w^2).  The work is the point-based symmetric scatter PB-SYM
+ * (Section 3.2, Algorithm 3): per event, a spatial invariant K_s[X][Y] and a
+ * temporal invariant K_t[T] whose outer product is added over the event's
+ * cylinder.  On the GPU the sum over events inside a voxel tile is evaluated as
+ * a rank-k contraction C[xy][t] = sum_k K_s[xy][k] K_t[k][t].
+ *
+ * Conventions shared by every entry point:
+ *  - Events are n rows of three doubles (x, y, t), row-major, in domain units.
+ *    The pointer may be host memory (pageable or pinned) or device memory of
+ *    the context's device; the library detects which.
+ *  - The grid is row-major [gx][gy][gt] binary32, T fastest (the stkde[X][Y][T]
+ *    array of Algorithms 1-3), gx*gy*gt floats.
+ *  - Bandwidths hs, ht are in domain units (hs in the units of x and y, ht in
+ *    the units of t), as in the density equation.
+ *  - Every event counts in n, including events outside the grid; cylinder
+ *    voxels outside the grid are dropped.  n = 0 yields an all-zero grid.
+ *  - The caller owns the events and the output buffer; the context owns its
+ *    workspace, which grows on demand and is freed by stkde_destroy.
+ *  - Calls are ordered on the context's stream and return once the work is
+ *    enqueued.  Argument errors are reported synchronously, before any launch.
+ *    Errors found on the device (non-finite coordinates, a bounded wait that
+ *    gave up) are latched and returned by stkde_synchronize, or by the next
+ *    call that synchronizes.
+ *  - A context is not thread-safe: use one per host thread.
+ */
+#ifndef STKDE_H
+#define STKDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define STKDE_API __attribute__((visibility("default")))
+#else
+#define STKDE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stkde_ctx stkde_ctx;
+
+typedef enum {
+    STKDE_OK = 0,
+    STKDE_ERR_INVALID_ARGUMENT = 1, /* bad pointer, size, bandwidth or resolution */
+    STKDE_ERR_OOM = 2,              /* a device allocation failed; no work was enqueued */
+    STKDE_ERR_CUDA = 3,             /* a CUDA runtime call failed */
+    STKDE_ERR_TIMEOUT = 4,          /* a device-side bounded wait gave up */
+    STKDE_ERR_UNSUPPORTED = 5,      /* e.g. no sm_103a device, or a form not built */
+    STKDE_ERR_NONFINITE = 6         /* an event coordinate was NaN or infinite */
+} stkde_status;
+
+/* How the sum over events is evaluated.  Every form writes each voxel of the
+ * grid exactly once, except STKDE_FORM_SCATTER. */
+typedef enum {
+    /* tcgen05 tensor cores: K_s and K_t split into bf16 hi + lo parts, three
+     * products (hi*hi + hi*lo + lo*hi) accumulated in fp32 in tensor memory. */
+    STKDE_FORM_TENSOR_BF16X3 = 0,
+    /* the same with fp16 hi + lo parts (11-bit significands). */
+    STKDE_FORM_TENSOR_FP16X3 = 1,
+    /* fp32 CUDA cores, per-voxel accumulation in registers. */
+    STKDE_FORM_FP32 = 2,
+    /* plain port of Algorithm 3: one block per event, atomic adds into a
+     * zeroed grid.  Baseline only: the summation order, and so the last bits,
+     * vary from run to run. */
+    STKDE_FORM_SCATTER = 3
+} stkde_form;
+
+/* Kernel constants (Section 2.1). */
+typedef enum {
+    STKDE_KERNEL_PRINTED = 0,   /* c_s = pi/2, c_t = 3/4, as printed */
+    STKDE_KERNEL_UNIT_MASS = 1  /* c_s = 24/(13 pi), c_t = 3/4: the density integrates to 1 */
+} stkde_kernel_constants;
+
+typedef struct {
+    int device;            /* CUDA device ordinal */
+    void* stream;          /* cudaStream_t the work is ordered on; NULL = legacy default stream */
+    int form;              /* stkde_form */
+    int kernel_constants;  /* stkde_kernel_constants */
+    int t_block;           /* voxels of T per tile: 0 = automatic, else a multiple of 16, <= 256 */
+    int slab;              /* T extent of an event bin: 0 = automatic, else >= 1 */
+    int profile;           /* 1: time each phase with CUDA events (see stkde_phase_times) */
+} stkde_options;
+
+typedef struct {
+    double x0, y0, t0;     /* domain origin: the corner of voxel (0, 0, 0) */
+    double sres, tres;     /* voxel size in space (x and y) and in time, > 0 */
+    int64_t gx, gy, gt;    /* grid size in voxels, >= 1 each */
+} stkde_grid;
+
+/* Fills *opt with the defaults: device 0, legacy stream, tensor bf16x3 form,
+ * printed constants, automatic tiling, no profiling. */
+STKDE_API void stkde_default_options(stkde_options* opt);
+
+/* Creates a context on opt->device (opt may be NULL for the defaults).
+ * Returns STKDE_ERR_UNSUPPORTED if the device is not compute capability 10.3. */
+STKDE_API stkde_status stkde_create(stkde_ctx** ctx, const stkde_options* opt);
+
+/* Section 2.1 density of n events on `grid`, bandwidths hs and ht, written to
+ * `out` (gx*gy*gt binary32, row-major [X][Y][T]).  `out` may be device memory
+ * of the context's device or host memory; with host memory the result is
+ * computed into a context-owned device buffer and copied back on the stream
+ * (pinned memory: asynchronously; pageable memory: the call returns after the
+ * copy).  `points` may be NULL only when n == 0.
+ * Errors: INVALID_ARGUMENT (NULL pointers, n < 0 or n >= 2^31, non-positive or
+ * non-finite hs, ht, sres, tres, a grid dimension < 1 or >= 2^31, or an
+ * origin that is not finite), OOM (workspace), CUDA. */
+STKDE_API stkde_status stkde_compute(stkde_ctx* ctx, const double* points, int64_t n,
+                           const stkde_grid* grid, double hs, double ht, float* out);
+
+/* One problem of a batch. */
+typedef struct {
+    const double* points;  /* n x 3 doubles, host or device */
+    int64_t n;
+    stkde_grid grid;
+    double hs, ht;
+    float* out;            /* device memory, gx*gy*gt binary32 */
+} stkde_problem;
+
+/* Computes `count` independent problems with the tensor (or fp32) tile kernel
+ * in one persistent launch whose work queue holds the tiles of all problems,
+ * heaviest first.  Each result equals the problem computed alone with the same
+ * form.  Outputs must be device memory. */
+STKDE_API stkde_status stkde_compute_batch(stkde_ctx* ctx, const stkde_problem* problems, int count);
+
+/* Number of (event, in-grid voxel) pairs inside the bandwidth cylinder
+ * (spatial test strict, temporal inclusive): the voxel-point updates of the
+ * problem.  Synchronous; FP64 arithmetic on the re-centred binary32 events. */
+STKDE_API stkde_status stkde_count_updates(stkde_ctx* ctx, const double* points, int64_t n,
+                                 const stkde_grid* grid, double hs, double ht,
+                                 uint64_t* count);
+
+/* Waits for the context's stream and returns the first latched device error,
+ * clearing it. */
+STKDE_API stkde_status stkde_synchronize(stkde_ctx* ctx);
+
+/* With options.profile = 1: fills ms[0..k) with the durations of the phases of
+ * the last stkde_compute (0 re-centre, 1 binning sort, 2 bin boundaries and
+ * gather, 3 tile kernel) and returns k; waits for the stream.  Returns 0 when
+ * profiling is off. */
+STKDE_API int stkde_phase_times(stkde_ctx* ctx, float* ms, int cap);
+
+/* Number of library kernels the last stkde_compute enqueued (0 for a NULL ctx). */
+STKDE_API int stkde_last_launch_count(stkde_ctx* ctx);
+
+/* Frees the context and its workspace (waits for its stream first). */
+STKDE_API void stkde_destroy(stkde_ctx* ctx);
+
+/* Static description of a status code. */
+STKDE_API const char* stkde_status_string(stkde_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STKDE_H */

@@ -65,7 +65,7 @@ def lib():
         l.oracle_vb_voxels.argtypes = [P, dp, i64, dp, i64, dp]
         l.oracle_pb.argtypes = [P, dp, i64, dp, dp]
         l.oracle_pb_box.argtypes = [P, dp, i64, i64, i64, i64, i64, i64, i64, dp, dp]
-        l.oracle_pb_boxes.argtypes = [P, dp, i64, dp, i64, dp, dp]
+        l.oracle_pb_boxes.argtypes = [P, dp, i64, dp, i64, dp, dp, dp]
         l.oracle_count_updates.argtypes = [P, dp, i64, dp]
         l.oracle_max_threads.argtypes = []
         for f in ("oracle_vb", "oracle_vb_voxels", "oracle_pb", "oracle_pb_box",
@@ -126,17 +126,19 @@ def pb(points, p: Params, with_slack: bool = False):
     return (out, slack) if with_slack else out
 
 
-def pb_boxes(points, p: Params, boxes, with_slack: bool = True):
+def pb_boxes(points, p: Params, boxes, with_slack: bool = True, pair_counts: bool = False):
     """Algorithm 2 restricted to boxes (bx0, bx1, by0, by1, bt0, bt1); returns a
-    list of (values, slack) arrays shaped like each box."""
+    list of (values, slack) arrays shaped like each box, plus the per-box count
+    of in-cylinder (event, voxel) pairs when ``pair_counts``."""
     a = _pts(points)
     b = np.ascontiguousarray(np.asarray(boxes, dtype=np.int64).reshape(-1, 6))
     sizes = (b[:, 1] - b[:, 0]) * (b[:, 3] - b[:, 2]) * (b[:, 5] - b[:, 4])
     tot = int(sizes.sum())
     out = np.empty(tot, dtype=np.float64)
     slack = np.empty(tot, dtype=np.float64) if with_slack else None
+    npairs = np.zeros(b.shape[0], dtype=np.uint64)
     rc = lib().oracle_pb_boxes(ctypes.byref(p), _ptr(a), a.shape[0], _ptr(b), b.shape[0],
-                               _ptr(out), _ptr(slack) if with_slack else None)
+                               _ptr(out), _ptr(slack) if with_slack else None, _ptr(npairs))
     if rc != 0:
         raise ValueError("box outside the grid or empty")
     res, off = [], 0
@@ -146,7 +148,7 @@ def pb_boxes(points, p: Params, boxes, with_slack: bool = True):
         res.append((out[off:off + sz].reshape(shp),
                     slack[off:off + sz].reshape(shp) if with_slack else None))
         off += sz
-    return res
+    return (res, npairs) if pair_counts else res
 
 
 def count_updates(points, p: Params) -> int:

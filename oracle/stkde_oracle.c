@@ -190,12 +190,14 @@ static int event_box(double pc, double hhat, int64_t lo_clip, int64_t hi_clip,
  * which a binary32 evaluation may legitimately decide the other way. */
 static void pb_box(const oracle_params* p, const double* pts, int64_t n,
                    int64_t bx0, int64_t bx1, int64_t by0, int64_t by1,
-                   int64_t bt0, int64_t bt1, double* box, double* slack) {
+                   int64_t bt0, int64_t bt1, double* box, double* slack, uint64_t* npairs) {
     const int64_t ny = by1 - by0, nt = bt1 - bt0;
     const size_t cells = (size_t)(bx1 - bx0) * (size_t)ny * (size_t)nt;
     memset(box, 0, sizeof(double) * cells);
     if (slack) memset(slack, 0, sizeof(double) * cells);
+    if (npairs) *npairs = 0;
     if (n == 0) return;
+    uint64_t pairs = 0;
     const double hsv = p->hs / p->sres, htv = p->ht / p->tres;   /* bandwidths in voxels */
     const double nrm = norm_factor(p, n);
     for (int64_t i = 0; i < n; ++i) {
@@ -219,12 +221,14 @@ static void pb_box(const oracle_params* p, const double* pts, int64_t n,
                     const double w = ((double)T + p->sample_off - pt) / htv;
                     if (!(fabs(w) <= 1.0)) continue;
                     const double term = ks * k_t(p, w) * nrm;
+                    pairs += (uint64_t)inside;
                     if (inside) box[base + (size_t)(T - bt0)] += term;
                     if (tie && slack) slack[base + (size_t)(T - bt0)] += fabs(term);
                 }
             }
         }
     }
+    if (npairs) *npairs = pairs;
 }
 
 /* Full grid by PB.  OpenMP over X-slabs: each thread owns whole X planes and
@@ -236,7 +240,7 @@ int oracle_pb(const oracle_params* p, const double* pts, int64_t n, double* out,
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t X = 0; X < gx; ++X) {
         const size_t off = (size_t)X * (size_t)p->gy * (size_t)p->gt;
-        pb_box(p, pts, n, X, X + 1, 0, p->gy, 0, p->gt, out + off, slack ? slack + off : NULL);
+        pb_box(p, pts, n, X, X + 1, 0, p->gy, 0, p->gt, out + off, slack ? slack + off : NULL, NULL);
     }
     return 0;
 }
@@ -248,14 +252,16 @@ int oracle_pb_box(const oracle_params* p, const double* pts, int64_t n,
     if (bx0 < 0 || by0 < 0 || bt0 < 0 || bx1 > p->gx || by1 > p->gy || bt1 > p->gt ||
         bx0 >= bx1 || by0 >= by1 || bt0 >= bt1)
         return 1;
-    pb_box(p, pts, n, bx0, bx1, by0, by1, bt0, bt1, box, slack);
+    pb_box(p, pts, n, bx0, bx1, by0, by1, bt0, bt1, box, slack, NULL);
     return 0;
 }
 
 /* Many boxes at once, one OpenMP task per box (boxes[6*j..6*j+5] =
- * bx0,bx1,by0,by1,bt0,bt1; outputs packed one after another). */
+ * bx0,bx1,by0,by1,bt0,bt1; outputs packed one after another).  npairs[j], if
+ * given, receives the number of in-cylinder (event, voxel) pairs of box j. */
 int oracle_pb_boxes(const oracle_params* p, const double* pts, int64_t n,
-                    const int64_t* boxes, int64_t nbox, double* out, double* slack) {
+                    const int64_t* boxes, int64_t nbox, double* out, double* slack,
+                    uint64_t* npairs) {
     set_threads(p);
     int64_t* offs = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nbox + 1));
     if (!offs) return 2;
@@ -270,7 +276,7 @@ int oracle_pb_boxes(const oracle_params* p, const double* pts, int64_t n,
     for (int64_t j = 0; j < nbox; ++j) {
         const int64_t* b = boxes + 6 * j;
         pb_box(p, pts, n, b[0], b[1], b[2], b[3], b[4], b[5], out + offs[j],
-               slack ? slack + offs[j] : NULL);
+               slack ? slack + offs[j] : NULL, npairs ? npairs + j : NULL);
     }
     free(offs);
     return 0;

@@ -1,0 +1,74 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stkde {
+
+// Tile footprint in the plane: TX rows of X by TY columns of Y = 128 voxels,
+// one tensor-memory lane (one accumulator row) per voxel.
+constexpr int TX = 16;
+constexpr int TY = 8;
+constexpr int TILE_XY = TX * TY;
+
+// Device error word bits.
+constexpr int ERRBIT_NONFINITE = 1;
+constexpr int ERRBIT_TIMEOUT = 2;
+constexpr int ERRBIT_BOUNDS = 4;
+
+// Everything a launch needs about one problem.  Host computes it in FP64 and
+// rounds the kernel's FP32 constants once.
+struct Plan {
+    // grid
+    int gx, gy, gt;
+    // bandwidths in voxels (FP32) and their reciprocals
+    float hsv, htv, inv_hs, inv_ht;
+    // kernel constants and normalisation 1/(n hs^2 ht) in domain units
+    float cs, ct, norm;
+    // event binning: cells = xy tiles, slabs of `slab` voxels in T
+    int ntx, nty, slab, nslab;
+    uint32_t nkeys;          // ntx*nty*nslab; key value nkeys marks an event that reaches no voxel
+    int key_bits;
+    // T blocks of the tile kernels
+    int tblock, ntb;
+    int64_t nitems;          // ntx * nty * ntb
+    int n;                   // events
+};
+
+// Per-problem device buffers (views into the context's workspace).
+struct Bins {
+    const float4* ev;        // re-centred events sorted by key: (x', y', t', bits(original index))
+    const uint32_t* start;   // start[k] = first sorted position with key >= k, k in [0, nkeys]
+};
+
+// ----------------------------------------------------------------- prep.cu
+// K0: re-centre (FP64) and cast to FP32, compute each event's bin key.
+void launch_recentre(const double* pts, int n, double x0, double y0, double t0, double sres,
+                     double tres, const Plan& pl, float4* ev, uint32_t* keys, uint32_t* idx,
+                     int* err, cudaStream_t st);
+// Stable LSD radix sort of (key, idx) pairs; result lands in keys/idx (tmp buffers used).
+size_t radix_sort_temp_bytes(int n);
+void launch_radix_sort(uint32_t* keys, uint32_t* idx, uint32_t* keys_tmp, uint32_t* idx_tmp,
+                       uint32_t* block_hist, int n, int key_bits, cudaStream_t st);
+// start[k] = lower_bound(sorted keys, k) for k in [0, nkeys]; gather events in sorted order.
+void launch_bounds_gather(const uint32_t* sorted_keys, const uint32_t* sorted_idx,
+                          const float4* ev, int n, uint32_t nkeys, uint32_t* start,
+                          float4* ev_sorted, cudaStream_t st);
+// Exact update count (FP64 on the binary32 re-centred events).
+// hsv, htv: FP64 bandwidths in voxels.
+void launch_count_updates(const float4* ev, int n, const Plan& pl, double hsv, double htv,
+                          unsigned long long* count, cudaStream_t st);
+
+// ------------------------------------------------------------ tile_fp32.cu
+void launch_tile_fp32(const Plan& pl, const Bins& b, float* out, int* err, cudaStream_t st);
+
+// -------------------------------------------------------------- scatter.cu
+void launch_scatter(const Plan& pl, const float4* ev, float* out, cudaStream_t st);
+
+// -------------------------------------------------------------- tile_tc.cu
+// Returns false if the form is not available in this build.
+bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int fp16,
+                    cudaStream_t st);
+
+}  // namespace stkde

@@ -1,0 +1,275 @@
+// Event preparation: re-centre and cast (K0), bin by (T slab, xy cell) with a
+// stable LSD radix sort (K1-K3), bin boundaries and the sorted event array.
+//
+// The binning realises the subdomain assignment of PB-SYM-DD (Section 4.2,
+// Algorithm 5): an xy tile must see every event whose cylinder box intersects
+// it.  Instead of replicating each event into every subdomain it touches, each
+// event is stored once, in the bin of its own (slab, cell); a tile then reads
+// the contiguous runs of bins around it.  Bins are ordered (slab, cell x,
+// cell y), so for one slab and one cell row x the cells y_lo..y_hi form a
+// single contiguous run of events.
+#include "internal.cuh"
+
+namespace stkde {
+
+// ------------------------------------------------------------------- K0 ---
+
+__global__ void k_recentre(const double* __restrict__ pts, int n, double x0, double y0,
+                           double t0, double sres, double tres, int by_recip, double isres,
+                           double itres, Plan pl, float4* __restrict__ ev,
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ idx,
+                           int* __restrict__ err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = pts[3 * (size_t)i + 0];
+    const double y = pts[3 * (size_t)i + 1];
+    const double t = pts[3 * (size_t)i + 2];
+    // Re-centre on the grid origin in FP64 (the only FP64 step of the path), then
+    // round to binary32.  Division unless the resolution is a power of two, where
+    // multiplying by the exact reciprocal gives the same bits.
+    double px, py, pt;
+    if (by_recip) {
+        px = (x - x0) * isres;
+        py = (y - y0) * isres;
+        pt = (t - t0) * itres;
+    } else {
+        px = (x - x0) / sres;
+        py = (y - y0) / sres;
+        pt = (t - t0) / tres;
+    }
+    const float fx = __double2float_rn(px);
+    const float fy = __double2float_rn(py);
+    const float ft = __double2float_rn(pt);
+    uint32_t key = pl.nkeys;  // reaches no voxel
+    if (!(isfinite(x) && isfinite(y) && isfinite(t))) {
+        atomicOr(err, ERRBIT_NONFINITE);
+    } else if (fx > -pl.hsv - 1.0f && fx < (float)pl.gx + pl.hsv + 1.0f &&
+               fy > -pl.hsv - 1.0f && fy < (float)pl.gy + pl.hsv + 1.0f &&
+               ft > -pl.htv - 1.0f && ft < (float)pl.gt + pl.htv + 1.0f) {
+        // Clamping moves an event outside the grid into the nearest edge cell or
+        // slab, which is no farther from any in-grid tile than the event is.
+        const int cx = min(max((int)floorf(fx * (1.0f / TX)), 0), pl.ntx - 1);
+        const int cy = min(max((int)floorf(fy * (1.0f / TY)), 0), pl.nty - 1);
+        const int s = min(max((int)floorf(ft / (float)pl.slab), 0), pl.nslab - 1);
+        key = ((uint32_t)s * (uint32_t)pl.ntx + (uint32_t)cx) * (uint32_t)pl.nty + (uint32_t)cy;
+    }
+    ev[i] = make_float4(fx, fy, ft, __int_as_float(i));
+    keys[i] = key;
+    idx[i] = (uint32_t)i;
+}
+
+void launch_recentre(const double* pts, int n, double x0, double y0, double t0, double sres,
+                     double tres, const Plan& pl, float4* ev, uint32_t* keys, uint32_t* idx,
+                     int* err, cudaStream_t st) {
+    if (n <= 0) return;
+    int e;
+    const bool p2 = (frexp(sres, &e) == 0.5) && (frexp(tres, &e) == 0.5);
+    k_recentre<<<(n + 255) / 256, 256, 0, st>>>(pts, n, x0, y0, t0, sres, tres, p2 ? 1 : 0,
+                                               1.0 / sres, 1.0 / tres, pl, ev, keys, idx, err);
+}
+
+// ---------------------------------------------------------- radix sort ---
+// LSD radix sort, 8-bit digits.  Each pass: per-block digit histograms, one
+// exclusive scan over [digit][block], then a stable scatter in which a block
+// ranks its keys round by round (256 keys a round, warp-level match for equal
+// digits, warps combined in order), so equal digits keep their input order.
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+constexpr int RS_BINS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+__global__ void __launch_bounds__(RS_THREADS)
+k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[RS_BINS];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * RS_TILE;
+#pragma unroll
+    for (int j = 0; j < RS_ROUNDS; ++j) {
+        const int p = base + j * RS_THREADS + threadIdx.x;
+        if (p < n) atomicAdd(&h[(keys[p] >> shift) & (RS_BINS - 1)], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of `total` counts in place, one block of 1024 threads, each
+// owning a contiguous chunk.
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ a, int total) {
+    __shared__ uint32_t part[1024];
+    const int per = (total + 1023) / 1024;
+    const int lo = threadIdx.x * per;
+    const int hi = min(lo + per, total);
+    uint32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += a[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;  // exclusive prefix of this chunk
+    for (int i = lo; i < hi; ++i) {
+        const uint32_t c = a[i];
+        a[i] = run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ iin,
+             uint32_t* __restrict__ kout, uint32_t* __restrict__ iout, int n, int shift,
+             const uint32_t* __restrict__ offs) {
+    __shared__ uint32_t run[RS_BINS];
+    __shared__ uint32_t wc[RS_WARPS][RS_BINS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    run[tid] = offs[(size_t)tid * gridDim.x + blockIdx.x];
+    const int base = blockIdx.x * RS_TILE;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int j = 0; j < RS_ROUNDS; ++j) {
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) wc[w][tid] = 0;
+        __syncthreads();
+        const int p = base + j * RS_THREADS + tid;
+        const bool valid = p < n;
+        const uint32_t k = valid ? kin[p] : 0u;
+        const uint32_t d = valid ? ((k >> shift) & (RS_BINS - 1)) : (uint32_t)RS_BINS;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) wc[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t r = run[tid];
+#pragma unroll
+            for (int w = 0; w < RS_WARPS; ++w) {
+                const uint32_t c = wc[w][tid];
+                wc[w][tid] = r;
+                r += c;
+            }
+            run[tid] = r;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = wc[warp][d] + rank;
+            kout[pos] = k;
+            iout[pos] = iin[p];
+        }
+        __syncthreads();
+    }
+}
+
+size_t radix_sort_temp_bytes(int n) {
+    const int nb = (n + RS_TILE - 1) / RS_TILE;
+    return (size_t)RS_BINS * (size_t)(nb > 0 ? nb : 1) * sizeof(uint32_t);
+}
+
+void launch_radix_sort(uint32_t* keys, uint32_t* idx, uint32_t* keys_tmp, uint32_t* idx_tmp,
+                       uint32_t* block_hist, int n, int key_bits, cudaStream_t st) {
+    if (n <= 1) return;
+    const int nb = (n + RS_TILE - 1) / RS_TILE;
+    const int passes = (key_bits + 7) / 8;
+    uint32_t *ka = keys, *ia = idx, *kb = keys_tmp, *ib = idx_tmp;
+    for (int ps = 0; ps < passes; ++ps) {
+        const int shift = 8 * ps;
+        k_rs_hist<<<nb, RS_THREADS, 0, st>>>(ka, n, shift, block_hist);
+        k_rs_scan<<<1, 1024, 0, st>>>(block_hist, RS_BINS * nb);
+        k_rs_scatter<<<nb, RS_THREADS, 0, st>>>(ka, ia, kb, ib, n, shift, block_hist);
+        uint32_t* t = ka; ka = kb; kb = t;
+        t = ia; ia = ib; ib = t;
+    }
+    if (ka != keys) {
+        cudaMemcpyAsync(keys, ka, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(idx, ia, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    }
+}
+
+// ------------------------------------------------ bounds and gather ---
+
+__global__ void k_bounds(const uint32_t* __restrict__ keys, int n, uint32_t nkeys,
+                         uint32_t* __restrict__ start) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > nkeys) return;
+    int lo = 0, hi = n;  // first position with keys[pos] >= k
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keys[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    start[k] = (uint32_t)lo;
+}
+
+__global__ void k_gather(const uint32_t* __restrict__ idx, const float4* __restrict__ ev, int n,
+                         float4* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) out[p] = ev[idx[p]];
+}
+
+void launch_bounds_gather(const uint32_t* sorted_keys, const uint32_t* sorted_idx,
+                          const float4* ev, int n, uint32_t nkeys, uint32_t* start,
+                          float4* ev_sorted, cudaStream_t st) {
+    const uint32_t nk = nkeys + 1;
+    k_bounds<<<(nk + 255) / 256, 256, 0, st>>>(sorted_keys, n, nkeys, start);
+    if (n > 0) k_gather<<<(n + 255) / 256, 256, 0, st>>>(sorted_idx, ev, n, ev_sorted);
+}
+
+// --------------------------------------------------------- update count ---
+// Exact count of (event, in-grid voxel) pairs inside the cylinder, FP64 on the
+// binary32 events.  Per event: the T count times the xy count; along each X row
+// the inside set is an interval in Y (the disk is convex), located by a square
+// root estimate and then settled by exact tests at both ends.
+
+__device__ __forceinline__ bool inside_xy(double du, double py, int Y, double hs) {
+    const double dv = ((double)Y + 0.5 - py) / hs;
+    return du * du + dv * dv < 1.0;
+}
+
+__global__ void k_count(const float4* __restrict__ ev, int n, int gx, int gy, int gt, double hs,
+                        double ht, unsigned long long* __restrict__ count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long c = 0;
+    if (i < n) {
+        const float4 e = ev[i];
+        const double px = e.x, py = e.y, pt = e.z;
+        if (isfinite(px) && isfinite(py) && isfinite(pt) && fabs(px) < 1e9 && fabs(py) < 1e9 &&
+            fabs(pt) < 1e9) {
+            const long long Ht = (long long)ceil(ht), Hs = (long long)ceil(hs);
+            const long long Ti = (long long)floor(pt), Xi = (long long)floor(px);
+            const long long Yi = (long long)floor(py);
+            long long nt = 0;
+            for (long long T = max(0LL, Ti - Ht); T <= min((long long)gt - 1, Ti + Ht); ++T) {
+                const double w = ((double)T + 0.5 - pt) / ht;
+                nt += fabs(w) <= 1.0;
+            }
+            long long nxy = 0;
+            if (nt > 0) {
+                const long long ylo0 = max(0LL, Yi - Hs), yhi0 = min((long long)gy - 1, Yi + Hs);
+                for (long long X = max(0LL, Xi - Hs); X <= min((long long)gx - 1, Xi + Hs); ++X) {
+                    const double du = ((double)X + 0.5 - px) / hs;
+                    const double r2 = 1.0 - du * du;
+                    if (r2 <= 0.0 || ylo0 > yhi0) continue;
+                    const double hw = sqrt(r2) * hs;
+                    long long lo = max(ylo0, (long long)floor(py - 0.5 - hw) - 1);
+                    long long hi = min(yhi0, (long long)ceil(py - 0.5 + hw) + 1);
+                    while (lo <= hi && !inside_xy(du, py, (int)lo, hs)) ++lo;
+                    while (hi >= lo && !inside_xy(du, py, (int)hi, hs)) --hi;
+                    if (hi >= lo) nxy += hi - lo + 1;
+                }
+            }
+            c = (unsigned long long)(nxy * nt);
+        }
+    }
+    // warp reduce then one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+void launch_count_updates(const float4* ev, int n, const Plan& pl, double hsv, double htv,
+                          unsigned long long* count, cudaStream_t st) {
+    if (n <= 0) return;
+    k_count<<<(n + 255) / 256, 256, 0, st>>>(ev, n, pl.gx, pl.gy, pl.gt, hsv, htv, count);
+}
+
+}  // namespace stkde

@@ -1,0 +1,406 @@
+// C ABI of the library (include/stkde.h): argument checking, the per-problem
+// plan, the context-owned workspace and the launch sequence
+//   K0 re-centre -> binning sort -> bin bounds + gather -> tile kernel.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/stkde.h"
+#include "internal.cuh"
+
+using namespace stkde;
+
+namespace {
+
+constexpr int MAX_PHASES = 5;
+constexpr uint32_t MAX_KEYS = 1u << 25;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct stkde_ctx {
+    stkde_options opt;
+    cudaStream_t stream;
+    int device;
+    int sm_count;
+    void* ws = nullptr;        // workspace
+    size_t ws_bytes = 0;
+    float* out_tmp = nullptr;  // device result buffer for host outputs
+    size_t out_tmp_bytes = 0;
+    int* d_err = nullptr;
+    unsigned long long* d_count = nullptr;
+    cudaEvent_t ev[MAX_PHASES + 1];
+    int nphase = 0;
+    bool events_ok = false;
+    int launches = 0;          // kernels enqueued by the last compute call
+};
+
+namespace {
+
+struct Workspace {
+    double* pts;
+    float4* ev;
+    float4* ev_sorted;
+    uint32_t *keys, *idx, *keys_tmp, *idx_tmp, *hist, *start;
+};
+
+// Carves the workspace for n events and nkeys bins; returns the bytes needed.
+size_t carve(void* base, int n, uint32_t nkeys, bool host_points, Workspace* w) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* p = base ? static_cast<char*>(base) + off : nullptr;
+        off = align_up(off + bytes, 256);
+        return p;
+    };
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    Workspace t;
+    t.pts = reinterpret_cast<double*>(take(host_points ? 24 * nn : 0));
+    t.ev = reinterpret_cast<float4*>(take(16 * nn));
+    t.ev_sorted = reinterpret_cast<float4*>(take(16 * nn));
+    t.keys = reinterpret_cast<uint32_t*>(take(4 * nn));
+    t.idx = reinterpret_cast<uint32_t*>(take(4 * nn));
+    t.keys_tmp = reinterpret_cast<uint32_t*>(take(4 * nn));
+    t.idx_tmp = reinterpret_cast<uint32_t*>(take(4 * nn));
+    t.hist = reinterpret_cast<uint32_t*>(take(radix_sort_temp_bytes(n)));
+    t.start = reinterpret_cast<uint32_t*>(take(4 * ((size_t)nkeys + 1)));
+    if (w) *w = t;
+    return off;
+}
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+stkde_status check_problem(const double* points, int64_t n, const stkde_grid* g, double hs,
+                           double ht) {
+    if (!g) return STKDE_ERR_INVALID_ARGUMENT;
+    if (n < 0 || n >= (int64_t)1 << 31) return STKDE_ERR_INVALID_ARGUMENT;
+    if (n > 0 && !points) return STKDE_ERR_INVALID_ARGUMENT;
+    if (!finite_pos(hs) || !finite_pos(ht) || !finite_pos(g->sres) || !finite_pos(g->tres))
+        return STKDE_ERR_INVALID_ARGUMENT;
+    if (!isfinite(g->x0) || !isfinite(g->y0) || !isfinite(g->t0)) return STKDE_ERR_INVALID_ARGUMENT;
+    const int64_t lim = (int64_t)1 << 31;
+    if (g->gx < 1 || g->gy < 1 || g->gt < 1 || g->gx >= lim || g->gy >= lim || g->gt >= lim)
+        return STKDE_ERR_INVALID_ARGUMENT;
+    // the grid must be addressable: gx*gy*gt < 2^60 voxels
+    const double vox = (double)g->gx * (double)g->gy * (double)g->gt;
+    if (vox >= 1.0e18) return STKDE_ERR_INVALID_ARGUMENT;
+    const double hsv = hs / g->sres, htv = ht / g->tres;
+    if (!(hsv < 1.0e6) || !(htv < 1.0e6)) return STKDE_ERR_INVALID_ARGUMENT;
+    return STKDE_OK;
+}
+
+Plan make_plan(const stkde_ctx* c, int64_t n, const stkde_grid* g, double hs, double ht,
+               int slab_opt) {
+    Plan p{};
+    p.gx = (int)g->gx; p.gy = (int)g->gy; p.gt = (int)g->gt;
+    const double hsv = hs / g->sres, htv = ht / g->tres;
+    p.hsv = (float)hsv; p.htv = (float)htv;
+    p.inv_hs = (float)(g->sres / hs);
+    p.inv_ht = (float)(g->tres / ht);
+    const double pi = 3.14159265358979323846;
+    p.cs = (float)(c->opt.kernel_constants == STKDE_KERNEL_UNIT_MASS ? 24.0 / (13.0 * pi) : pi / 2.0);
+    p.ct = 0.75f;
+    p.norm = n > 0 ? (float)(1.0 / ((double)n * hs * hs * ht)) : 0.0f;
+    p.ntx = (p.gx + TX - 1) / TX;
+    p.nty = (p.gy + TY - 1) / TY;
+    int slab = slab_opt > 0 ? slab_opt : 4;
+    slab = slab < p.gt ? slab : p.gt;
+    while (true) {
+        const uint64_t ns = (uint64_t)((p.gt + slab - 1) / slab);
+        const uint64_t nk = ns * (uint64_t)p.ntx * (uint64_t)p.nty;
+        if (nk <= MAX_KEYS || slab >= p.gt) break;
+        slab *= 2;
+    }
+    p.slab = slab;
+    p.nslab = (p.gt + slab - 1) / slab;
+    const uint64_t nk = (uint64_t)p.nslab * (uint64_t)p.ntx * (uint64_t)p.nty;
+    p.nkeys = (uint32_t)(nk < 0xffffffffull ? nk : 0xffffffffull);
+    int bits = 1;
+    while (bits < 32 && ((uint64_t)1 << bits) <= (uint64_t)p.nkeys) ++bits;
+    p.key_bits = bits;
+    p.n = (int)n;
+    p.tblock = 0; p.ntb = 0; p.nitems = 0;
+    return p;
+}
+
+stkde_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return STKDE_OK;
+    if (e == cudaErrorMemoryAllocation) return STKDE_ERR_OOM;
+    return STKDE_ERR_CUDA;
+}
+
+stkde_status ensure_ws(stkde_ctx* c, size_t bytes) {
+    if (bytes <= c->ws_bytes) return STKDE_OK;
+    cudaStreamSynchronize(c->stream);
+    if (c->ws) cudaFree(c->ws);
+    c->ws = nullptr; c->ws_bytes = 0;
+    const size_t want = align_up(bytes + bytes / 8, 1 << 20);
+    cudaError_t e = cudaMalloc(&c->ws, want);
+    if (e != cudaSuccess) { cudaGetLastError(); c->ws = nullptr; return STKDE_ERR_OOM; }
+    c->ws_bytes = want;
+    return STKDE_OK;
+}
+
+// Is p a pointer the device can use directly?  Host (pageable or pinned) memory
+// is copied instead.  -1: device memory of another device.
+int pointer_kind(const void* p, int device) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return 0; }
+    if (a.type == cudaMemoryTypeDevice) return a.device == device ? 1 : -1;
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    return 0;
+}
+
+void mark(stkde_ctx* c) {
+    if (c->opt.profile && c->events_ok && c->nphase <= MAX_PHASES)
+        cudaEventRecord(c->ev[c->nphase++], c->stream);
+}
+
+// Enqueues one problem whose events are already on the device.  The result goes
+// to the device buffer `out`.
+stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stkde_grid* g,
+                     const Workspace& w, float* out) {
+    cudaStream_t st = c->stream;
+    const int form = c->opt.form;
+    const int n = pl.n;
+    mark(c);
+    launch_recentre(dpts, n, g->x0, g->y0, g->t0, g->sres, g->tres, pl, w.ev, w.keys, w.idx,
+                    c->d_err, st);
+    c->launches += 1;
+    if (form == STKDE_FORM_SCATTER) {
+        mark(c);
+        cudaMemsetAsync(out, 0, sizeof(float) * (size_t)pl.gx * pl.gy * pl.gt, st);
+        mark(c);
+        mark(c);
+        launch_scatter(pl, w.ev, out, st);
+        c->launches += 1;
+        mark(c);
+        return cuda_status(cudaGetLastError());
+    }
+    mark(c);
+    launch_radix_sort(w.keys, w.idx, w.keys_tmp, w.idx_tmp, w.hist, n, pl.key_bits, st);
+    c->launches += n > 1 ? 3 * ((pl.key_bits + 7) / 8) : 0;
+    mark(c);
+    launch_bounds_gather(w.keys, w.idx, w.ev, n, pl.nkeys, w.start, w.ev_sorted, st);
+    c->launches += 2;
+    mark(c);
+    Bins b{w.ev_sorted, w.start};
+    if (form == STKDE_FORM_FP32) {
+        launch_tile_fp32(pl, b, out, c->d_err, st);
+    } else {
+        if (!launch_tile_tc(pl, b, out, c->d_err, form == STKDE_FORM_TENSOR_FP16X3 ? 1 : 0, st))
+            return STKDE_ERR_UNSUPPORTED;
+    }
+    c->launches += 1;
+    mark(c);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+void stkde_default_options(stkde_options* opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->device = 0;
+    opt->stream = nullptr;
+    opt->form = STKDE_FORM_TENSOR_BF16X3;
+    opt->kernel_constants = STKDE_KERNEL_PRINTED;
+}
+
+const char* stkde_status_string(stkde_status s) {
+    switch (s) {
+        case STKDE_OK: return "ok";
+        case STKDE_ERR_INVALID_ARGUMENT: return "invalid argument";
+        case STKDE_ERR_OOM: return "out of device memory";
+        case STKDE_ERR_CUDA: return "CUDA runtime error";
+        case STKDE_ERR_TIMEOUT: return "device-side wait timed out";
+        case STKDE_ERR_UNSUPPORTED: return "unsupported device or form";
+        case STKDE_ERR_NONFINITE: return "non-finite event coordinate";
+    }
+    return "unknown status";
+}
+
+stkde_status stkde_create(stkde_ctx** out, const stkde_options* opt) {
+    if (!out) return STKDE_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    stkde_options o;
+    if (opt) o = *opt; else stkde_default_options(&o);
+    if (o.form < STKDE_FORM_TENSOR_BF16X3 || o.form > STKDE_FORM_SCATTER)
+        return STKDE_ERR_INVALID_ARGUMENT;
+    if (o.kernel_constants != STKDE_KERNEL_PRINTED && o.kernel_constants != STKDE_KERNEL_UNIT_MASS)
+        return STKDE_ERR_INVALID_ARGUMENT;
+    if (o.t_block != 0 && (o.t_block < 16 || o.t_block > 256 || o.t_block % 16 != 0))
+        return STKDE_ERR_INVALID_ARGUMENT;
+    if (o.slab < 0) return STKDE_ERR_INVALID_ARGUMENT;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return STKDE_ERR_UNSUPPORTED; }
+    if (o.device < 0 || o.device >= ndev) return STKDE_ERR_INVALID_ARGUMENT;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, o.device) != cudaSuccess) return STKDE_ERR_CUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return STKDE_ERR_UNSUPPORTED;
+    if (cudaSetDevice(o.device) != cudaSuccess) return STKDE_ERR_CUDA;
+    stkde_ctx* c = new (std::nothrow) stkde_ctx;
+    if (!c) return STKDE_ERR_OOM;
+    c->opt = o;
+    c->stream = static_cast<cudaStream_t>(o.stream);
+    c->device = o.device;
+    c->sm_count = prop.multiProcessorCount;
+    if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->d_err) cudaFree(c->d_err);
+        delete c;
+        return STKDE_ERR_OOM;
+    }
+    cudaMemset(c->d_err, 0, sizeof(int));
+    c->events_ok = true;
+    for (int i = 0; i <= MAX_PHASES; ++i)
+        if (cudaEventCreate(&c->ev[i]) != cudaSuccess) c->events_ok = false;
+    cudaDeviceSynchronize();
+    *out = c;
+    return STKDE_OK;
+}
+
+void stkde_destroy(stkde_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (c->ws) cudaFree(c->ws);
+    if (c->out_tmp) cudaFree(c->out_tmp);
+    if (c->d_err) cudaFree(c->d_err);
+    if (c->d_count) cudaFree(c->d_count);
+    for (int i = 0; i <= MAX_PHASES; ++i)
+        if (c->events_ok) cudaEventDestroy(c->ev[i]);
+    delete c;
+}
+
+stkde_status stkde_synchronize(stkde_ctx* c) {
+    if (!c) return STKDE_ERR_INVALID_ARGUMENT;
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int h = 0;
+    e = cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (h) cudaMemset(c->d_err, 0, sizeof(int));
+    if (h & ERRBIT_NONFINITE) return STKDE_ERR_NONFINITE;
+    if (h & ERRBIT_TIMEOUT) return STKDE_ERR_TIMEOUT;
+    if (h & ERRBIT_BOUNDS) return STKDE_ERR_CUDA;
+    return STKDE_OK;
+}
+
+stkde_status stkde_compute(stkde_ctx* c, const double* points, int64_t n, const stkde_grid* g,
+                           double hs, double ht, float* out) {
+    if (!c || !out) return STKDE_ERR_INVALID_ARGUMENT;
+    stkde_status s = check_problem(points, n, g, hs, ht);
+    if (s != STKDE_OK) return s;
+    if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
+    const int okind = pointer_kind(out, c->device);
+    if (okind < 0) return STKDE_ERR_INVALID_ARGUMENT;
+    const size_t grid_bytes = sizeof(float) * (size_t)g->gx * (size_t)g->gy * (size_t)g->gt;
+    float* dout = out;
+    if (okind == 0) {  // host output: compute into the context's buffer, copy back
+        if (grid_bytes > c->out_tmp_bytes) {
+            cudaStreamSynchronize(c->stream);
+            if (c->out_tmp) cudaFree(c->out_tmp);
+            c->out_tmp = nullptr; c->out_tmp_bytes = 0;
+            if (cudaMalloc(&c->out_tmp, grid_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return STKDE_ERR_OOM;
+            }
+            c->out_tmp_bytes = grid_bytes;
+        }
+        dout = c->out_tmp;
+    }
+    c->nphase = 0;
+    c->launches = 0;
+    if (n == 0) {
+        cudaMemsetAsync(dout, 0, grid_bytes, c->stream);
+    } else {
+        if (c->opt.form == STKDE_FORM_SCATTER) {
+            const double htv = ht / g->tres;
+            if (2.0 * ceil(htv) + 1.0 > 12000.0) return STKDE_ERR_UNSUPPORTED;
+        }
+        const int pkind = pointer_kind(points, c->device);
+        if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
+        const Plan pl = make_plan(c, n, g, hs, ht, c->opt.slab);
+        Workspace w;
+        const size_t need = carve(nullptr, (int)n, pl.nkeys, pkind == 0, nullptr);
+        s = ensure_ws(c, need);
+        if (s != STKDE_OK) return s;
+        carve(c->ws, (int)n, pl.nkeys, pkind == 0, &w);
+        const double* dpts = points;
+        if (pkind == 0) {
+            cudaError_t e = cudaMemcpyAsync(w.pts, points, 24 * (size_t)n, cudaMemcpyHostToDevice,
+                                            c->stream);
+            if (e != cudaSuccess) return cuda_status(e);
+            dpts = w.pts;
+        }
+        s = enqueue(c, dpts, pl, g, w, dout);
+        if (s != STKDE_OK) return s;
+    }
+    if (okind == 0) {
+        cudaError_t e = cudaMemcpyAsync(out, dout, grid_bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int count) {
+    if (!c || (count > 0 && !probs) || count < 0) return STKDE_ERR_INVALID_ARGUMENT;
+    return STKDE_ERR_UNSUPPORTED;
+}
+
+stkde_status stkde_count_updates(stkde_ctx* c, const double* points, int64_t n,
+                                 const stkde_grid* g, double hs, double ht, uint64_t* count) {
+    if (!c || !count) return STKDE_ERR_INVALID_ARGUMENT;
+    stkde_status s = check_problem(points, n, g, hs, ht);
+    if (s != STKDE_OK) return s;
+    *count = 0;
+    if (n == 0) return STKDE_OK;
+    if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
+    const int pkind = pointer_kind(points, c->device);
+    if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
+    const Plan pl = make_plan(c, n, g, hs, ht, c->opt.slab);
+    Workspace w;
+    s = ensure_ws(c, carve(nullptr, (int)n, pl.nkeys, pkind == 0, nullptr));
+    if (s != STKDE_OK) return s;
+    carve(c->ws, (int)n, pl.nkeys, pkind == 0, &w);
+    const double* dpts = points;
+    if (pkind == 0) {
+        cudaMemcpyAsync(w.pts, points, 24 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+        dpts = w.pts;
+    }
+    launch_recentre(dpts, (int)n, g->x0, g->y0, g->t0, g->sres, g->tres, pl, w.ev, w.keys, w.idx,
+                    c->d_err, c->stream);
+    cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream);
+    launch_count_updates(w.ev, (int)n, pl, hs / g->sres, ht / g->tres, c->d_count, c->stream);
+    unsigned long long h = 0;
+    cudaMemcpyAsync(&h, c->d_count, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    *count = h;
+    return STKDE_OK;
+}
+
+int stkde_last_launch_count(stkde_ctx* c) { return c ? c->launches : 0; }
+
+int stkde_phase_times(stkde_ctx* c, float* ms, int cap) {
+    if (!c || !c->opt.profile || !c->events_ok || c->nphase < 2) return 0;
+    cudaSetDevice(c->device);
+    cudaEventSynchronize(c->ev[c->nphase - 1]);
+    int k = 0;
+    for (int i = 0; i + 1 < c->nphase && k < cap; ++i, ++k) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]);
+        ms[k] = t;
+    }
+    return k;
+}
+
+}  // extern "C"

@@ -1,0 +1,203 @@
+// K4: fp32 CUDA-core tile kernel.
+//
+// PB-SYM (Section 3.2, Algorithm 3) evaluated owner-computes: one CTA owns an
+// output tile of 16 x 8 voxels in the plane by 64 voxels of T and is the only
+// writer of those voxels, so no atomics are needed and every voxel sums its
+// events in one fixed order (the bin order), which makes the result
+// bit-reproducible.  The CTA walks the event bins around the tile (the
+// subdomain assignment of Algorithm 5, done by reading neighbouring bins instead
+// of replicating events), keeps the events whose cylinder reaches the tile,
+// builds each kept event's temporal invariant K_t over the tile's T range in
+// shared memory, and every thread adds K_s(voxel) * K_t[T] into the 32
+// accumulators it holds in registers.  Each voxel is written once, zeros
+// included, so the grid needs no separate initialisation (the Theta(G) init of
+// Algorithm 2 becomes part of the store stream).
+#include "internal.cuh"
+
+namespace stkde {
+
+namespace {
+
+constexpr int F_THREADS = 256;   // 128 voxels x 2 halves of the T block
+constexpr int F_TB = 64;         // voxels of T per tile
+constexpr int F_HALF = 32;       // T accumulators per thread
+constexpr int F_BATCH = 128;     // events per K_t table
+constexpr int F_BUF = F_BATCH + F_THREADS;
+
+struct TileGeom {
+    int X0, X1, Y0, Y1, T0, T1;
+    float rx0, rx1, ry0, ry1;     // in-grid voxel-centre rectangle of the tile
+    int cx_lo, cx_hi, cy_lo, cy_hi, s_lo, s_hi;
+};
+
+__device__ __forceinline__ TileGeom tile_geom(const Plan& pl, int tx, int ty, int tb, int tblock) {
+    TileGeom g;
+    g.X0 = tx * TX; g.X1 = min(g.X0 + TX, pl.gx);
+    g.Y0 = ty * TY; g.Y1 = min(g.Y0 + TY, pl.gy);
+    g.T0 = tb * tblock; g.T1 = min(g.T0 + tblock, pl.gt);
+    g.rx0 = (float)g.X0 + 0.5f; g.rx1 = (float)g.X1 - 0.5f;
+    g.ry0 = (float)g.Y0 + 0.5f; g.ry1 = (float)g.Y1 - 0.5f;
+    const float m = 0.01f;  // widen: binning only needs a superset
+    g.cx_lo = max(0, (int)floorf((g.rx0 - pl.hsv - m) * (1.0f / TX)));
+    g.cx_hi = min(pl.ntx - 1, (int)floorf((g.rx1 + pl.hsv + m) * (1.0f / TX)));
+    g.cy_lo = max(0, (int)floorf((g.ry0 - pl.hsv - m) * (1.0f / TY)));
+    g.cy_hi = min(pl.nty - 1, (int)floorf((g.ry1 + pl.hsv + m) * (1.0f / TY)));
+    const float t0 = (float)g.T0 + 0.5f - pl.htv - m, t1 = (float)g.T1 - 0.5f + pl.htv + m;
+    g.s_lo = max(0, (int)floorf(t0 / (float)pl.slab));
+    g.s_hi = min(pl.nslab - 1, (int)floorf(t1 / (float)pl.slab));
+    return g;
+}
+
+// Does the event's cylinder reach a voxel centre of the tile?  A superset test
+// (bandwidths widened by 0.01 voxel); events that pass but reach nothing add zeros.
+__device__ __forceinline__ bool reaches(const Plan& pl, const TileGeom& g, float4 e) {
+    const float dx = fmaxf(fmaxf(g.rx0 - e.x, e.x - g.rx1), 0.0f);
+    const float dy = fmaxf(fmaxf(g.ry0 - e.y, e.y - g.ry1), 0.0f);
+    const float r = pl.hsv + 0.01f;
+    const bool xy = dx * dx + dy * dy < r * r;
+    const bool t = (e.z + pl.htv + 0.01f > (float)g.T0 + 0.5f) &&
+                   (e.z - pl.htv - 0.01f < (float)g.T1 - 0.5f);
+    return xy && t;
+}
+
+__global__ void __launch_bounds__(F_THREADS, 2)
+k_tile_fp32(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ start,
+            float* __restrict__ out) {
+    __shared__ float4 buf[F_BUF];
+    __shared__ __align__(16) float ktab[F_BATCH][F_TB];
+    __shared__ int2 win[F_BATCH];
+    __shared__ int wcount[F_THREADS / 32];
+    __shared__ int s_count;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t item = blockIdx.x;
+    const int ty = (int)(item % pl.nty);
+    const int tx = (int)((item / pl.nty) % pl.ntx);
+    const int tb = (int)(item / ((int64_t)pl.nty * pl.ntx));
+    const TileGeom g = tile_geom(pl, tx, ty, tb, F_TB);
+
+    const int m = tid & (TILE_XY - 1), h = tid >> 7;
+    const int X = g.X0 + m / TY, Y = g.Y0 + m % TY;
+    const float xc = (float)X + 0.5f, yc = (float)Y + 0.5f;
+
+    float acc[F_HALF];
+#pragma unroll
+    for (int c = 0; c < F_HALF; ++c) acc[c] = 0.0f;
+
+    if (tid == 0) s_count = 0;
+    __syncthreads();
+
+    // Adds the events buf[off, off+cnt) into the accumulators.
+    auto process = [&](int off, int cnt) {
+        // temporal invariants K_t[T] over the tile's T block (Algorithm 3's bar)
+        for (int q = tid; q < cnt * F_TB; q += F_THREADS) {
+            const int j = q / F_TB, c = q % F_TB;
+            const float w = ((float)(g.T0 + c) + 0.5f - buf[off + j].z) * pl.inv_ht;
+            ktab[j][c] = pl.ct * fmaxf(fmaf(-w, w, 1.0f), 0.0f);
+        }
+        for (int j = tid; j < cnt; j += F_THREADS) {
+            const float pt = buf[off + j].z;
+            win[j] = make_int2((int)floorf(pt - 0.5f - pl.htv) - g.T0 - 1,
+                               (int)ceilf(pt - 0.5f + pl.htv) - g.T0 + 1);
+        }
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+            const float4 e = buf[off + j];
+            const float u = (xc - e.x) * pl.inv_hs;
+            const float v = (yc - e.y) * pl.inv_hs;
+            const float s = fmaf(u, u, v * v);
+            const float a = s < 1.0f ? pl.cs * fmaf(-u, u, 1.0f) * fmaf(-v, v, 1.0f) : 0.0f;
+            if (!__any_sync(0xffffffffu, a != 0.0f)) continue;
+            const int2 wj = win[j];
+#pragma unroll
+            for (int gq = 0; gq < F_HALF / 16; ++gq) {
+                const int c0 = h * F_HALF + gq * 16;
+                if (wj.x <= c0 + 15 && wj.y >= c0) {
+                    const float4* kr = reinterpret_cast<const float4*>(&ktab[j][c0]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 k4 = kr[q];
+                        acc[gq * 16 + 4 * q + 0] = fmaf(a, k4.x, acc[gq * 16 + 4 * q + 0]);
+                        acc[gq * 16 + 4 * q + 1] = fmaf(a, k4.y, acc[gq * 16 + 4 * q + 1]);
+                        acc[gq * 16 + 4 * q + 2] = fmaf(a, k4.z, acc[gq * 16 + 4 * q + 2]);
+                        acc[gq * 16 + 4 * q + 3] = fmaf(a, k4.w, acc[gq * 16 + 4 * q + 3]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    };
+
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int s = g.s_lo; s <= g.s_hi; ++s) {
+        for (int cx = g.cx_lo; cx <= g.cx_hi; ++cx) {
+            const uint32_t kb = ((uint32_t)s * (uint32_t)pl.ntx + (uint32_t)cx) * (uint32_t)pl.nty;
+            const int a = (int)start[kb + g.cy_lo];
+            const int b = (int)start[kb + g.cy_hi + 1];
+            for (int base = a; base < b; base += F_THREADS) {
+                const int p = base + tid;
+                float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+                bool keep = false;
+                if (p < b) {
+                    e = ev[p];
+                    keep = reaches(pl, g, e);
+                }
+                const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0) wcount[warp] = __popc(bal);
+                __syncthreads();
+                int pre = s_count, tot = 0;
+#pragma unroll
+                for (int w = 0; w < F_THREADS / 32; ++w) {
+                    const int c = wcount[w];
+                    pre += w < warp ? c : 0;
+                    tot += c;
+                }
+                if (keep) buf[pre + __popc(bal & lt)] = e;
+                const int cnt = s_count + tot;
+                __syncthreads();
+                if (tid == 0) s_count = cnt;
+                if (cnt >= F_BATCH) {
+                    const int full = (cnt / F_BATCH) * F_BATCH;
+                    for (int off = 0; off < full; off += F_BATCH) process(off, F_BATCH);
+                    const int rem = cnt - full;  // < F_BATCH <= full: no overlap
+                    for (int q = tid; q < rem; q += F_THREADS) buf[q] = buf[full + q];
+                    if (tid == 0) s_count = rem;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    const int rem = s_count;
+    if (rem > 0) process(0, rem);
+
+    if (X < pl.gx && Y < pl.gy) {
+        const int Tb = g.T0 + h * F_HALF;
+        float* dst = out + ((int64_t)X * pl.gy + Y) * (int64_t)pl.gt + Tb;
+        const int nvalid = min(F_HALF, pl.gt - Tb);
+        if (nvalid == F_HALF && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+            for (int q = 0; q < F_HALF / 4; ++q)
+                reinterpret_cast<float4*>(dst)[q] =
+                    make_float4(acc[4 * q] * pl.norm, acc[4 * q + 1] * pl.norm,
+                                acc[4 * q + 2] * pl.norm, acc[4 * q + 3] * pl.norm);
+        } else {
+#pragma unroll
+            for (int c = 0; c < F_HALF; ++c)
+                if (c < nvalid) dst[c] = acc[c] * pl.norm;
+        }
+    }
+}
+
+}  // namespace
+
+void launch_tile_fp32(const Plan& pl, const Bins& b, float* out, int* err, cudaStream_t st) {
+    (void)err;
+    Plan p = pl;
+    p.tblock = F_TB;
+    p.ntb = (pl.gt + F_TB - 1) / F_TB;
+    const int64_t items = (int64_t)p.ntx * p.nty * p.ntb;
+    if (items <= 0) return;
+    k_tile_fp32<<<(unsigned)items, F_THREADS, 0, st>>>(p, b.ev, b.start, out);
+}
+
+}  // namespace stkde

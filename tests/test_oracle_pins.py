@@ -281,3 +281,14 @@ def test_tie_slack_marks_only_wall_pairs():
     assert slack[13, 14, 10] > 0.0
     assert slack[10, 10, 10] == 0.0
     assert (slack > 0).sum() < (out > 0).sum()
+
+
+def test_box_pair_counts_add_up_to_the_update_count():
+    """Pair counts of boxes that tile the grid sum to the whole-grid update count."""
+    rng = np.random.default_rng(31)
+    pts = synth.tiny(rng, 40, 24, 20, 18)
+    p = oracle.params(24, 20, 18, 3.2, 2.6)
+    boxes = [(x, min(24, x + 7), y, min(20, y + 9), t, min(18, t + 10))
+             for x in range(0, 24, 7) for y in range(0, 20, 9) for t in range(0, 18, 10)]
+    _, counts = oracle.pb_boxes(pts, p, boxes, pair_counts=True)
+    assert int(counts.sum()) == oracle.count_updates(pts, p)
