@@ -144,25 +144,30 @@ def tile_boxes(w, seed=0):
 
 
 def oracle_sample(w, seconds, seed=0, calib=None):
-    """Times the FP64 oracle (Algorithm 2 on sampled tiles, all host cores) for
-    about `seconds`; returns (pairs, elapsed, boxes, results)."""
+    """Times the FP64 oracle (Algorithm 2 on random tiles, all host cores) for
+    about `seconds`, growing the sample in batches; returns (pairs, elapsed,
+    boxes, results, seconds per box)."""
     import oracle
     p = oracle.params(w.gx, w.gy, w.gt, w.hs, w.ht, x0=w.x0, y0=w.y0, t0=w.t0, sres=w.sres,
                       tres=w.tres)
     boxes = tile_boxes(w, seed)
-    if calib is None:
+    done, pairs, elapsed, res = 0, 0, 0.0, []
+    per_box = calib
+    while done < len(boxes) and elapsed < seconds:
+        if per_box is None:
+            k = 16
+        else:
+            k = int(max(1, round((seconds - elapsed) / max(per_box, 1e-6))))
+        sel = boxes[done:done + k]
         t = time.perf_counter()
-        _, c = oracle.pb_boxes(w.points, p, boxes[:4], with_slack=False, pair_counts=True)
-        dt = max(time.perf_counter() - t, 1e-3)
-        per_box = dt / 4
-    else:
-        per_box = calib
-    k = int(max(1, min(len(boxes), round(seconds / per_box))))
-    sel = boxes[:k]
-    t = time.perf_counter()
-    res, counts = oracle.pb_boxes(w.points, p, sel, with_slack=True, pair_counts=True)
-    dt = time.perf_counter() - t
-    return int(counts.sum()), dt, sel, res, dt / k
+        r, c = oracle.pb_boxes(w.points, p, sel, with_slack=True, pair_counts=True)
+        dt = time.perf_counter() - t
+        res.extend(r)
+        pairs += int(c.sum())
+        elapsed += dt
+        done += len(sel)
+        per_box = elapsed / done
+    return pairs, elapsed, boxes[:done], res, per_box
 
 
 # ------------------------------------------------------------- reference ---

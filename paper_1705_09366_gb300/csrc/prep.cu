@@ -69,8 +69,9 @@ void launch_recentre(const double* pts, int n, double x0, double y0, double t0, 
 }
 
 // ---------------------------------------------------------- radix sort ---
-// LSD radix sort, 8-bit digits.  Each pass: per-block digit histograms, one
-// exclusive scan over [digit][block], then a stable scatter in which a block
+// LSD radix sort, 8-bit digits.  Each pass: per-block digit histograms, an
+// exclusive scan over the blocks per digit (one CTA per digit) plus the digit
+// totals, then a stable scatter in which a block
 // ranks its keys round by round (256 keys a round, warp-level match for equal
 // digits, warps combined in order), so equal digits keep their input order.
 
@@ -95,39 +96,63 @@ k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift, uint32_t* __restr
     hist[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of `total` counts in place, one block of 1024 threads, each
-// owning a contiguous chunk.
-__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ a, int total) {
-    __shared__ uint32_t part[1024];
-    const int per = (total + 1023) / 1024;
-    const int lo = threadIdx.x * per;
-    const int hi = min(lo + per, total);
-    uint32_t s = 0;
-    for (int i = lo; i < hi; ++i) s += a[i];
-    part[threadIdx.x] = s;
+// Exclusive scan of one digit's counts over the blocks, in place: one CTA per
+// digit, block-wide scan in tiles of RS_THREADS; the digit's total goes to
+// totals[digit].
+__global__ void __launch_bounds__(RS_THREADS)
+k_rs_scan_digit(uint32_t* __restrict__ hist, int nb, uint32_t* __restrict__ totals) {
+    __shared__ uint32_t wsum[RS_WARPS];
+    __shared__ uint32_t carry;
+    uint32_t* a = hist + (size_t)blockIdx.x * nb;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry = 0;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    for (int base = 0; base < nb; base += RS_THREADS) {
+        const int i = base + tid;
+        const uint32_t v = i < nb ? a[i] : 0u;
+        uint32_t x = v;  // inclusive warp scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
         __syncthreads();
-        part[threadIdx.x] += v;
+        uint32_t pre = carry;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) pre += w < warp ? wsum[w] : 0u;
+        if (i < nb) a[i] = pre + x - v;
+        __syncthreads();
+        if (tid == RS_THREADS - 1) carry = pre + x;
         __syncthreads();
     }
-    uint32_t run = part[threadIdx.x] - s;  // exclusive prefix of this chunk
-    for (int i = lo; i < hi; ++i) {
-        const uint32_t c = a[i];
-        a[i] = run;
-        run += c;
-    }
+    if (tid == 0) totals[blockIdx.x] = carry;
 }
 
 __global__ void __launch_bounds__(RS_THREADS)
 k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ iin,
              uint32_t* __restrict__ kout, uint32_t* __restrict__ iout, int n, int shift,
-             const uint32_t* __restrict__ offs) {
+             const uint32_t* __restrict__ offs, const uint32_t* __restrict__ totals) {
     __shared__ uint32_t run[RS_BINS];
     __shared__ uint32_t wc[RS_WARPS][RS_BINS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    run[tid] = offs[(size_t)tid * gridDim.x + blockIdx.x];
+    {
+        // base of this thread's digit = sum of the totals of smaller digits
+        const uint32_t t = totals[tid];
+        uint32_t x = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wc[0][warp] = x;
+        __syncthreads();
+        uint32_t pre = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) pre += w < warp ? wc[0][w] : 0u;
+        run[tid] = pre + x - t + offs[(size_t)tid * gridDim.x + blockIdx.x];
+        __syncthreads();
+    }
     const int base = blockIdx.x * RS_TILE;
     const uint32_t lt = (1u << lane) - 1u;
     for (int j = 0; j < RS_ROUNDS; ++j) {
@@ -164,7 +189,7 @@ k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ iin,
 
 size_t radix_sort_temp_bytes(int n) {
     const int nb = (n + RS_TILE - 1) / RS_TILE;
-    return (size_t)RS_BINS * (size_t)(nb > 0 ? nb : 1) * sizeof(uint32_t);
+    return ((size_t)RS_BINS * (size_t)(nb > 0 ? nb : 1) + RS_BINS) * sizeof(uint32_t);
 }
 
 void launch_radix_sort(uint32_t* keys, uint32_t* idx, uint32_t* keys_tmp, uint32_t* idx_tmp,
@@ -175,9 +200,10 @@ void launch_radix_sort(uint32_t* keys, uint32_t* idx, uint32_t* keys_tmp, uint32
     uint32_t *ka = keys, *ia = idx, *kb = keys_tmp, *ib = idx_tmp;
     for (int ps = 0; ps < passes; ++ps) {
         const int shift = 8 * ps;
+        uint32_t* totals = block_hist + (size_t)RS_BINS * nb;
         k_rs_hist<<<nb, RS_THREADS, 0, st>>>(ka, n, shift, block_hist);
-        k_rs_scan<<<1, 1024, 0, st>>>(block_hist, RS_BINS * nb);
-        k_rs_scatter<<<nb, RS_THREADS, 0, st>>>(ka, ia, kb, ib, n, shift, block_hist);
+        k_rs_scan_digit<<<RS_BINS, RS_THREADS, 0, st>>>(block_hist, nb, totals);
+        k_rs_scatter<<<nb, RS_THREADS, 0, st>>>(ka, ia, kb, ib, n, shift, block_hist, totals);
         uint32_t* t = ka; ka = kb; kb = t;
         t = ia; ia = ib; ib = t;
     }
