@@ -14,28 +14,33 @@
 //
 // The tensor cores round each accumulation step toward zero, so a long run of
 // steps into one accumulator drifts low.  The MMA thread therefore closes an
-// accumulator "segment" before any 16-column block of it has taken more than
-// FLUSH steps; the epilogue stores the first segment of a tile and adds later
-// ones to it in fp32 (round to nearest), which bounds the drift per segment.
+// accumulator "segment" before any 32-column block of it has taken more than a
+// fixed number of chunks; the epilogue stores the first segment of a tile and
+// adds later ones to it in fp32 (round to nearest), which bounds the drift.
 //
-// Persistent CTA per SM, warp-specialised, every hand-off through mbarriers:
-//   warp 0      MMA issue (one thread), tensor-memory allocation
-//   warp 1      loader: walks the tile's event bins and stages them into shared
-//               memory pages with cp.async.bulk (no multicast)
-//   warp 2      filter: keeps the events whose cylinder reaches the tile and
-//               appends them, in bin order, to a ring of 16-event chunk slots;
-//               a tile ends with a partial slot and an end-of-tile slot
-//   warps 3-10  generators: chunk slot j is built by generator j mod 8, alone,
-//               into its own operand stage: A = K_s and B = K_t as hi and lo
-//               16-bit tiles (B in column windows of up to 128)
-//   warps 11-14 epilogue: one per tensor-memory lane quarter; scales by
-//               1/(n hs^2 ht), writes each voxel of the tile (vector stores),
-//               adds later segments, zeroes the accumulator
+// Persistent CTA per SM, warp-specialised, every hand-off through mbarriers
+// (warp w runs on scheduler w % 4; the MMA thread shares its scheduler only
+// with the light loader and one epilogue warp):
+//   warp 0            MMA issue (one thread), tensor-memory allocation
+//   warp 4            loader: walks the tile's event bins and stages them, in
+//                     bin order, into 256-event shared-memory pages with
+//                     cp.async.bulk (no multicast), one copy per bin run, all
+//                     lanes issuing in parallel
+//   warps 1-3,5-7,9,10  generators: every generator reads every page; the
+//                     page's owner (page q: generator q mod 8) keeps the events
+//                     whose cylinder reaches the tile, compacting the page in
+//                     place, and chunk c of the page -- kept events 16c..16c+15
+//                     -- is built by generator (q + c) mod 8 in its own operand
+//                     stage: A = K_s and B = K_t as hi and lo 16-bit tiles (B in
+//                     column windows of up to 128)
+//   warps 12-15       epilogue: one per tensor-memory lane quarter; scales by
+//                     1/(n hs^2 ht), writes each voxel of the tile (vector
+//                     stores), adds later segments, zeroes the accumulator
 // Two accumulators of 256 columns let the epilogue of one segment overlap the
-// MMAs of the next.  The MMA thread consumes chunk slots in sequence order, so
-// every voxel sums its events in the same order on every run (bit-reproducible,
-// no global atomics).  The earliest unconsumed chunk can always be produced,
-// so no wait can close a cycle.
+// MMAs of the next.  The MMA thread consumes pages, and the chunks of a page, in
+// order, so every voxel sums its events in the same order on every run
+// (bit-reproducible, no global atomics).  The generator of the earliest
+// unconsumed chunk can always build it, so no wait can close a cycle.
 //
 // Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
 // kernel sets the timeout bit of the error word, every role leaves its loop,
@@ -57,15 +62,12 @@ constexpr int NACC = 2;            // accumulators (512 tensor-memory columns)
 constexpr int NGEN = 8;            // generator warps
 constexpr int NEPI = 4;            // epilogue warps
 constexpr int WARP_MMA = 0;
-constexpr int WARP_LOAD = 1;
-constexpr int WARP_FILT = 2;
-constexpr int WARP_GEN0 = 3;
-constexpr int WARP_EPI0 = WARP_GEN0 + NGEN;
-constexpr int NTHREADS = (WARP_EPI0 + NEPI) * 32;
+constexpr int WARP_LOAD = 4;
+constexpr int WARP_EPI0 = 12;
+constexpr int NTHREADS = 16 * 32;
 constexpr int PAGE = 256;          // events per staging page
-constexpr int NPAGES = 4;
+constexpr int NPAGES = 12;
 constexpr int CHUNK = 16;          // events per MMA (K of kind::f16)
-constexpr int RSLOTS = 32;         // chunk slots in the kept-event ring
 constexpr int NCAP = 128;          // T columns per operand stage (one column window)
 constexpr int TAB_ROW = 144;       // bytes per factor-table row (16 float2 + pad: no bank conflicts)
 constexpr uint64_t WAIT_NS = 2000000000ull;
@@ -77,32 +79,40 @@ constexpr uint32_t TAB_BYTES = 3584;                // x table, y table, t value
 constexpr uint32_t CORE_LBO = 128;  // next core matrix along K
 constexpr uint32_t CORE_SBO = 256;  // next core matrix along M / N
 
-// slot and stage header flags
-constexpr int F_CHUNK = 1, F_MORE = 2, F_END = 4, F_TERM = 8;
+// page and stage header flags
+constexpr int F_MMA = 1;        // stage holds operands for the MMA
+constexpr int F_PAGE_END = 2;   // last stage of a page
+constexpr int F_ITEM_END = 4;   // last page / stage of a tile
+constexpr int F_TERM = 8;       // page: no more tiles
+constexpr int F_MORE = 16;      // stage: another column window of the same chunk follows
+
+// generator index of a warp (-1: not a generator)
+__device__ __forceinline__ int gen_index(int warp) {
+    return (warp >= 1 && warp <= 3) ? warp - 1 : (warp >= 5 && warp <= 7) ? warp - 2
+         : (warp == 9 || warp == 10) ? warp - 3 : -1;
+}
 
 struct L {
     static constexpr uint32_t OFF_STAGE = 0;
     static constexpr uint32_t OFF_PAGES = OFF_STAGE + NGEN * STAGE_BYTES;
-    static constexpr uint32_t OFF_RING = OFF_PAGES + NPAGES * PAGE * 16;
-    static constexpr uint32_t OFF_RHDR = OFF_RING + RSLOTS * CHUNK * 16;
-    static constexpr uint32_t OFF_TAB = OFF_RHDR + RSLOTS * 16;
+    static constexpr uint32_t OFF_TAB = OFF_PAGES + NPAGES * PAGE * 16;
     static constexpr uint32_t OFF_SHDR = OFF_TAB + NGEN * TAB_BYTES;
     static constexpr uint32_t OFF_PMETA = OFF_SHDR + NGEN * 16;
-    static constexpr uint32_t OFF_DESC = OFF_PMETA + NPAGES * 16;
+    static constexpr uint32_t OFF_KEPT = OFF_PMETA + NPAGES * 16;
+    static constexpr uint32_t OFF_DESC = OFF_KEPT + NPAGES * 16;
     static constexpr uint32_t OFF_BAR = OFF_DESC + NACC * 16;
-    static constexpr int NBARS = 2 * NPAGES + 2 * RSLOTS + 2 * NGEN + 3 * NACC + 1;
+    static constexpr int NBARS = 3 * NPAGES + 2 * NGEN + 3 * NACC + 1;
     static constexpr uint32_t OFF_MISC = OFF_BAR + NBARS * 8;
     static constexpr uint32_t TOTAL = OFF_MISC + 16;
     __host__ __device__ static constexpr int pfull(int p) { return p; }
     __host__ __device__ static constexpr int pempty(int p) { return NPAGES + p; }
-    __host__ __device__ static constexpr int cfull(int s) { return 2 * NPAGES + s; }
-    __host__ __device__ static constexpr int cempty(int s) { return 2 * NPAGES + RSLOTS + s; }
-    __host__ __device__ static constexpr int sfull(int g) { return 2 * NPAGES + 2 * RSLOTS + g; }
-    __host__ __device__ static constexpr int sempty(int g) { return 2 * NPAGES + 2 * RSLOTS + NGEN + g; }
-    __host__ __device__ static constexpr int afull(int b) { return 2 * NPAGES + 2 * RSLOTS + 2 * NGEN + b; }
-    __host__ __device__ static constexpr int aempty(int b) { return 2 * NPAGES + 2 * RSLOTS + 2 * NGEN + NACC + b; }
-    __host__ __device__ static constexpr int dfull(int b) { return 2 * NPAGES + 2 * RSLOTS + 2 * NGEN + 2 * NACC + b; }
-    __host__ __device__ static constexpr int drain() { return 2 * NPAGES + 2 * RSLOTS + 2 * NGEN + 3 * NACC; }
+    __host__ __device__ static constexpr int pfilt(int p) { return 2 * NPAGES + p; }
+    __host__ __device__ static constexpr int sfull(int g) { return 3 * NPAGES + g; }
+    __host__ __device__ static constexpr int sempty(int g) { return 3 * NPAGES + NGEN + g; }
+    __host__ __device__ static constexpr int afull(int b) { return 3 * NPAGES + 2 * NGEN + b; }
+    __host__ __device__ static constexpr int aempty(int b) { return 3 * NPAGES + 2 * NGEN + NACC + b; }
+    __host__ __device__ static constexpr int dfull(int b) { return 3 * NPAGES + 2 * NGEN + 2 * NACC + b; }
+    __host__ __device__ static constexpr int drain() { return 3 * NPAGES + 2 * NGEN + 3 * NACC; }
     static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
     static_assert(TOTAL <= 227 * 1024, "shared memory budget");
     static_assert(TAB_BYTES >= (TX + TY) * TAB_ROW + CHUNK * 4, "table size");
@@ -174,7 +184,7 @@ __device__ __forceinline__ void decode_item(const Plan& pl, int64_t item, int& t
 template <bool FP16>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ start,
-          float* __restrict__ out, int* __restrict__ err, int64_t nitems, int flush_steps) {
+          float* __restrict__ out, int* __restrict__ err, int64_t nitems, int flush_chunks) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const uint32_t sb = ptx::smem_addr(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -184,11 +194,8 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
     if (threadIdx.x == 0) {
         for (int p = 0; p < NPAGES; ++p) {
             ptx::mbar_init(bar(L::pfull(p)), 1);
-            ptx::mbar_init(bar(L::pempty(p)), 1);
-        }
-        for (int s = 0; s < RSLOTS; ++s) {
-            ptx::mbar_init(bar(L::cfull(s)), 1);
-            ptx::mbar_init(bar(L::cempty(s)), 1);
+            ptx::mbar_init(bar(L::pempty(p)), NGEN);
+            ptx::mbar_init(bar(L::pfilt(p)), 1);
         }
         for (int g = 0; g < NGEN; ++g) {
             ptx::mbar_init(bar(L::sfull(g)), 1);
@@ -211,365 +218,335 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + L::OFF_MISC);
+    const int gi = gen_index(warp);
 
     if (warp == WARP_LOAD) {
         // ------------------------------------------------------------ loader
         uint32_t pg = 0, fill = 0;
         bool open = false, ok = true;
+        auto open_page = [&]() -> bool {
+            if (!wait_warp(c, bar(L::pempty(pg % NPAGES)), ((pg / NPAGES) & 1u) ^ 1u)) return false;
+            open = true;
+            fill = 0;
+            return true;
+        };
+        auto close_page = [&](int flags, int64_t item) {
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t p = pg % NPAGES;
+                ptx::sts_i4(sb + L::OFF_PMETA + p * 16,
+                            make_int4((int)fill, flags, (int)(item & 0xffffffff), (int)(item >> 32)));
+                ptx::mbar_arrive(bar(L::pfull(p)));
+            }
+            __syncwarp();
+            ++pg;
+            open = false;
+        };
         for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
             int tx, ty, tb;
             decode_item(pl, item, tx, ty, tb);
             const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
             const int ncx = g.cx_hi - g.cx_lo + 1;
             const int nr = (g.s_hi >= g.s_lo && ncx > 0) ? (g.s_hi - g.s_lo + 1) * ncx : 0;
-            for (int r0 = 0; r0 <= nr && ok; r0 += 32) {
-                uint32_t a = 0, b = 0;
+            for (int r0 = 0; r0 < nr && ok; r0 += 32) {
+                // 32 bin runs at a time: lane-parallel lengths, offsets by a warp scan
+                uint32_t a = 0, len = 0;
                 const int r = r0 + lane;
                 if (r < nr) {
                     const int s = g.s_lo + r / ncx, cx = g.cx_lo + r % ncx;
                     const uint32_t kb =
                         ((uint32_t)s * (uint32_t)pl.ntx + (uint32_t)cx) * (uint32_t)pl.nty;
                     a = start[kb + g.cy_lo];
-                    b = start[kb + g.cy_hi + 1];
+                    len = start[kb + g.cy_hi + 1] - a;
                 }
-                const int nj = min(32, nr - r0);
-                // nj <= 0 on the final pass: it only closes the tile's last page
-                for (int j = 0; j <= nj && ok; ++j) {
-                    uint32_t aj = 0, bj = 0;
-                    if (j < nj) {
-                        aj = __shfl_sync(0xffffffffu, a, j);
-                        bj = __shfl_sync(0xffffffffu, b, j);
-                    } else if (r0 + 32 <= nr) {
-                        break;  // not the final pass
-                    }
-                    const bool last = (j == nj) && (r0 + 32 > nr);
-                    while (aj < bj || last) {
-                        if (!open) {
-                            const uint32_t p = pg % NPAGES;
-                            if (!(ok = wait_warp(c, bar(L::pempty(p)), ((pg / NPAGES) & 1u) ^ 1u))) break;
-                            open = true;
-                            fill = 0;
-                        }
-                        const uint32_t p = pg % NPAGES;
-                        const uint32_t take = min(bj - aj, (uint32_t)PAGE - fill);
-                        if (take > 0 && lane == 0) {
-                            ptx::mbar_expect_tx(bar(L::pfull(p)), take * 16u);
-                            ptx::bulk_g2s(sb + L::OFF_PAGES + (p * PAGE + fill) * 16u, ev + aj,
-                                          take * 16u, bar(L::pfull(p)));
-                        }
-                        fill += take;
-                        aj += take;
-                        if (fill == (uint32_t)PAGE || (last && aj >= bj)) {
-                            if (lane == 0) {
-                                ptx::sts_i4(sb + L::OFF_PMETA + p * 16,
-                                            make_int4((int)fill, last && aj >= bj ? 1 : 0, 0, 0));
-                                ptx::mbar_arrive(bar(L::pfull(p)));
-                            }
-                            __syncwarp();
-                            ++pg;
-                            open = false;
-                            if (last && aj >= bj) break;
-                        }
-                    }
+                uint32_t incl = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
                 }
-            }
-        }
-        if (!ok) {
-            if (open) {
-                if (lane == 0) {
+                const uint32_t off = incl - len, tot = __shfl_sync(0xffffffffu, incl, 31);
+                uint32_t done = 0;
+                while (done < tot) {
+                    if (!open && !(ok = open_page())) break;
                     const uint32_t p = pg % NPAGES;
-                    ptx::sts_i4(sb + L::OFF_PMETA + p * 16, make_int4((int)fill, 1, 0, 0));
-                    ptx::mbar_arrive(bar(L::pfull(p)));
+                    const uint32_t take = min((uint32_t)PAGE - fill, tot - done);
+                    // this page takes pass positions [done, done + take); each lane copies
+                    // the part of its own run that falls there
+                    const uint32_t lo = max(off, done), hi = min(off + len, done + take);
+                    if (hi > lo) {
+                        ptx::mbar_expect_tx(bar(L::pfull(p)), (hi - lo) * 16u);
+                        ptx::bulk_g2s(sb + L::OFF_PAGES + (p * PAGE + fill + (lo - done)) * 16u,
+                                      ev + a + (lo - off), (hi - lo) * 16u, bar(L::pfull(p)));
+                    }
+                    fill += take;
+                    done += take;
+                    if (fill == (uint32_t)PAGE) close_page(0, item);
                 }
-                ++pg;
             }
+            if (!ok) break;
+            if (!open && !(ok = open_page())) break;
+            close_page(F_ITEM_END, item);  // the tile's last page, possibly empty
+        }
+        // termination page (every generator reads every page)
+        if (ok && (ok = open_page())) close_page(F_TERM, 0);
+        if (!ok) {
+            if (open) close_page(F_TERM, 0);
             for (uint32_t q = (pg > NPAGES ? pg - NPAGES : 0); q < pg; ++q)
                 drain_bar(bar(L::pfull(q % NPAGES)), (q / NPAGES) & 1u);
         }
-    } else if (warp == WARP_FILT) {
-        // ------------------------------------------------------------ filter
-        uint32_t pg = 0, kabs = 0, acq = 0, pub = 0;
-        bool ok = true;
+    } else if (gi >= 0) {
+        // -------------------------------------------------------- generators
+        // Every generator reads every page.  The page's owner (page q: generator
+        // q mod 8) keeps the events whose cylinder reaches the tile, compacting
+        // them in place; chunk c of page q (events 16c .. 16c+15 of the kept list)
+        // is then built by generator (q + c) mod 8 into its own stage.
+        const uint32_t tab = sb + L::OFF_TAB + gi * TAB_BYTES;
+        const uint32_t tabx = tab, taby = tab + TX * TAB_ROW, tt = tab + (TX + TY) * TAB_ROW;
+        const uint32_t stg = sb + L::OFF_STAGE + gi * STAGE_BYTES;
+        const uint32_t a_hi = stg, a_lo = stg + A_BYTES, b_hi = stg + 2 * A_BYTES,
+                       b_lo = b_hi + B_BYTES;
+        const uint32_t shdr = sb + L::OFF_SHDR + gi * 16;
         const uint32_t lt = (1u << lane) - 1u;
-        // makes ring slots [acq, upto] writable
-        auto acquire = [&](uint32_t upto) -> bool {
-            while (acq <= upto) {
-                if (!wait_warp(c, bar(L::cempty(acq % RSLOTS)), ((acq / RSLOTS) & 1u) ^ 1u))
-                    return false;
-                ++acq;
-            }
-            return true;
-        };
-        // publishes slot `pub` with `count` events
-        auto publish = [&](int count, int flags, int64_t item) {
+        const float csct = pl.cs * pl.ct;
+        uint32_t suse = 0;  // uses of this warp's stage
+        bool ok = true;
+        // hands the stage to the MMA thread
+        auto publish = [&](int c0, int ncols, int flags) {
+            if (lane == 0) ptx::sts_i4(shdr, make_int4(c0, ncols, flags, 0));
+            ptx::fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) {
-                const uint32_t s = pub % RSLOTS;
-                ptx::sts_i4(sb + L::OFF_RHDR + s * 16,
-                            make_int4(count, flags, (int)(item & 0xffffffff), (int)(item >> 32)));
-                ptx::mbar_arrive(bar(L::cfull(s)));
-            }
-            __syncwarp();
-            ++pub;
+            if (lane == 0) ptx::mbar_arrive(bar(L::sfull(gi)));
+            ++suse;
         };
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        for (uint32_t q = 0; ok; ++q) {
+            const uint32_t p = q % NPAGES;
+            const uint32_t ph = (q / NPAGES) & 1u;
+            const uint32_t pgb = sb + L::OFF_PAGES + p * PAGE * 16;
+            if (!(ok = wait_warp(c, bar(L::pfull(p)), ph))) break;
+            const int4 meta = ptx::lds_i4(sb + L::OFF_PMETA + p * 16);
+            if (meta.y & F_TERM) break;
+            const int64_t item = (int64_t)(uint32_t)meta.z | ((int64_t)meta.w << 32);
+            const int end = meta.y & F_ITEM_END;
             int tx, ty, tb;
             decode_item(pl, item, tx, ty, tb);
             const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
-            bool end = false;
-            while (!end && ok) {
-                const uint32_t p = pg % NPAGES;
-                if (!(ok = wait_warp(c, bar(L::pfull(p)), (pg / NPAGES) & 1u))) break;
-                const int4 meta = ptx::lds_i4(sb + L::OFF_PMETA + p * 16);
-                end = meta.y != 0;
-                for (int r = 0; r * 32 < meta.x && ok; ++r) {
+            const int X0 = g.X0, Y0 = g.Y0, T0 = g.T0, nbv = g.T1 - g.T0;
+            const int own = (int)(q % NGEN) == gi;
+            if (own) {
+                // keep the events whose cylinder reaches the tile, compacted in place
+                uint32_t kept = 0;
+                for (int r = 0; r * 32 < meta.x; ++r) {
                     const int slot = r * 32 + lane;
                     float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
                     bool keep = false;
                     if (slot < meta.x) {
-                        e = ptx::lds_f4(sb + L::OFF_PAGES + (p * PAGE + slot) * 16u);
+                        e = ptx::lds_f4(pgb + slot * 16u);
                         keep = reaches(pl, g, e);
                     }
                     const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-                    const uint32_t nk = __popc(bal);
-                    if (nk == 0) continue;
-                    if (!(ok = acquire((kabs + nk - 1) / CHUNK))) break;
-                    if (keep) {
-                        const uint32_t pos = (kabs + __popc(bal & lt)) % (RSLOTS * CHUNK);
-                        ptx::sts_f4(sb + L::OFF_RING + pos * 16, e);
-                    }
-                    kabs += nk;
-                    while (pub < kabs / CHUNK) publish(CHUNK, F_CHUNK, item);
+                    __syncwarp();
+                    if (keep) ptx::sts_f4(pgb + (kept + __popc(bal & lt)) * 16u, e);
+                    kept += __popc(bal);
+                    __syncwarp();
                 }
-                __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(bar(L::pempty(p)));
-                ++pg;
-            }
-            if (!ok) break;
-            if (kabs % CHUNK) {  // the tile's last, partial chunk
-                publish((int)(kabs % CHUNK), F_CHUNK, item);
-                kabs = pub * CHUNK;
-            }
-            if (!(ok = acquire(pub))) break;  // end-of-tile slot
-            publish(0, F_END, item);
-            kabs = pub * CHUNK;
-        }
-        // one termination slot per generator
-        for (int gq = 0; gq < NGEN && ok; ++gq) {
-            if (!(ok = acquire(pub))) break;
-            publish(0, F_TERM, 0);
-        }
-    } else if (warp >= WARP_GEN0 && warp < WARP_EPI0) {
-        // -------------------------------------------------------- generators
-        const int gw = warp - WARP_GEN0;
-        const uint32_t tab = sb + L::OFF_TAB + gw * TAB_BYTES;
-        const uint32_t tabx = tab, taby = tab + TX * TAB_ROW, tt = tab + (TX + TY) * TAB_ROW;
-        const uint32_t stg = sb + L::OFF_STAGE + gw * STAGE_BYTES;
-        const uint32_t a_hi = stg, a_lo = stg + A_BYTES, b_hi = stg + 2 * A_BYTES,
-                       b_lo = b_hi + B_BYTES;
-        const uint32_t shdr = sb + L::OFF_SHDR + gw * 16;
-        const float csct = pl.cs * pl.ct;
-        uint32_t suse = 0;  // uses of this warp's stage
-        bool ok = true;
-        for (uint32_t j = (uint32_t)gw; ok; j += NGEN) {
-            const uint32_t s = j % RSLOTS;
-            if (!(ok = wait_warp(c, bar(L::cfull(s)), (j / RSLOTS) & 1u))) break;
-            const int4 h = ptx::lds_i4(sb + L::OFF_RHDR + s * 16);
-            const int count = h.x;
-            float4 e = make_float4(1.0e30f, 1.0e30f, 1.0e30f, 0.f);
-            if (lane < count) e = ptx::lds_f4(sb + L::OFF_RING + (s * CHUNK + lane) * 16u);
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(bar(L::cempty(s)));
-            if (h.y & F_TERM) break;
-            if (h.y & F_END) {  // forward the end of the tile to the MMA thread
-                if (!(ok = wait_warp(c, bar(L::sempty(gw)), (suse & 1u) ^ 1u))) break;
                 if (lane == 0) {
-                    ptx::sts_i4(shdr, make_int4(0, 0, F_END, 0));
-                    ptx::mbar_arrive(bar(L::sfull(gw)));
+                    ptx::sts_i4(sb + L::OFF_KEPT + p * 16, make_int4((int)kept, 0, 0, 0));
+                    ptx::mbar_arrive(bar(L::pfilt(p)));
                 }
                 __syncwarp();
-                ++suse;
-                continue;
+            } else if (!(ok = wait_warp(c, bar(L::pfilt(p)), ph))) {
+                break;
             }
-            const int64_t item = (int64_t)(uint32_t)h.z | ((int64_t)h.w << 32);
-            int tx, ty, tb;
-            decode_item(pl, item, tx, ty, tb);
-            const int X0 = tx * TX, Y0 = ty * TY, T0 = tb * NB;
-            const int nbv = min(NB, pl.gt - T0);
-
-            // columns the events' T windows cover, clipped into the block (the
-            // filter's margin can keep an event whose window misses the block;
-            // its K_t values are zero anyway)
-            int lo = 0x7fffffff, hi = -1;
-            if (lane < count) {
-                lo = min(max((int)ceilf(e.z - 0.5f - pl.htv) - T0, 0), nbv - 1);
-                hi = min(max((int)floorf(e.z - 0.5f + pl.htv) - T0, lo), nbv - 1);
+            const int kept = ptx::lds_i4(sb + L::OFF_KEPT + p * 16).x;
+            const int nch = (kept + CHUNK - 1) / CHUNK;
+            if (nch == 0 && own) {  // nothing to add: just mark the page's end
+                if (!(ok = wait_warp(c, bar(L::sempty(gi)), (suse & 1u) ^ 1u))) break;
+                publish(0, 0, F_PAGE_END | end);
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-            }
-            const int c0 = lo & ~15;
-            const int cend = ((hi + 1) + 15) & ~15;  // exclusive, <= roundup16(nbv) <= NB
-
-            // factor tables of K_s: (u^2, 1-u^2) per x and (v^2, 1-v^2) per y
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int q = i * 32 + lane, x = q >> 4, k = q & 15;
-                const float ex = __shfl_sync(0xffffffffu, e.x, k);
-                const float du = ((float)(X0 + x) + 0.5f - ex) * pl.inv_hs;
-                const float u2 = du * du;
-                ptx::sts_f2(tabx + x * TAB_ROW + k * 8, make_float2(u2, 1.0f - u2));
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int q = i * 32 + lane, y = q >> 4, k = q & 15;
-                const float ey = __shfl_sync(0xffffffffu, e.y, k);
-                const float dv = ((float)(Y0 + y) + 0.5f - ey) * pl.inv_hs;
-                const float v2 = dv * dv;
-                ptx::sts_f2(taby + y * TAB_ROW + k * 8, make_float2(v2, 1.0f - v2));
-            }
-            if (lane < CHUNK) ptx::sts_f(tt + lane * 4, e.z);
-            __syncwarp();
-
-            if (!(ok = wait_warp(c, bar(L::sempty(gw)), (suse & 1u) ^ 1u))) break;
-            // A = K_s without c_s: row r = voxel (x = r / 8, y = r % 8); lane owns
-            // rows lane + 32 j, all with y = lane % 8
-#pragma unroll
-            for (int kg = 0; kg < 2; ++kg) {
-                float4 fy[4];
-#pragma unroll
-                for (int kp = 0; kp < 4; ++kp)
-                    fy[kp] = ptx::lds_f4(taby + (lane & 7) * TAB_ROW + (kg * 8 + 2 * kp) * 8);
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const int r = lane + 32 * jj;
-                    uint32_t ah[4], al[4];
-#pragma unroll
-                    for (int kp = 0; kp < 4; ++kp) {
-                        const float4 fx = ptx::lds_f4(tabx + (r >> 3) * TAB_ROW + (kg * 8 + 2 * kp) * 8);
-                        const float a0 = (fx.x + fy[kp].x < 1.0f) ? fx.y * fy[kp].y : 0.0f;
-                        const float a1 = (fx.z + fy[kp].z < 1.0f) ? fx.w * fy[kp].w : 0.0f;
-                        split2<FP16>(a0, a1, ah[kp], al[kp]);
-                    }
-                    const uint32_t off = (uint32_t)(r >> 3) * CORE_SBO + kg * CORE_LBO + (r & 7) * 16;
-                    ptx::sts_u4(a_hi + off, ah[0], ah[1], ah[2], ah[3]);
-                    ptx::sts_u4(a_lo + off, al[0], al[1], al[2], al[3]);
+            for (int ch = (int)((gi - (int)(q % NGEN) + NGEN) % NGEN); ch < nch && ok; ch += NGEN) {
+                const int count = min(CHUNK, kept - ch * CHUNK);
+                float4 e = make_float4(1.0e30f, 1.0e30f, 1.0e30f, 0.f);
+                if (lane < count) e = ptx::lds_f4(pgb + (ch * CHUNK + lane) * 16u);
+                // columns the events' T windows cover, clipped into the block (the
+                // filter's margin can keep an event whose window misses the block;
+                // its K_t values are zero anyway)
+                int lo = 0x7fffffff, hi = -1;
+                if (lane < count) {
+                    lo = min(max((int)ceilf(e.z - 0.5f - pl.htv) - T0, 0), nbv - 1);
+                    hi = min(max((int)floorf(e.z - 0.5f + pl.htv) - T0, lo), nbv - 1);
                 }
-            }
-            // B = c_s c_t (1 - w^2)_+ in column windows of up to NCAP
-            float tk[CHUNK];
 #pragma unroll
-            for (int k4 = 0; k4 < CHUNK / 4; ++k4) {
-                const float4 t4 = ptx::lds_f4(tt + k4 * 16);
-                tk[4 * k4] = t4.x; tk[4 * k4 + 1] = t4.y; tk[4 * k4 + 2] = t4.z; tk[4 * k4 + 3] = t4.w;
-            }
-            for (int cw = c0; cw < cend && ok; cw += NCAP) {
-                if (cw != c0 && !(ok = wait_warp(c, bar(L::sempty(gw)), (suse & 1u) ^ 1u))) break;
-                const int ncols = min(NCAP, cend - cw);
-                for (int n = lane; n < ncols; n += 32) {
-                    const float tc = (float)(T0 + cw + n) + 0.5f;
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                }
+                const int c0 = lo & ~15;
+                const int cend = ((hi + 1) + 15) & ~15;  // exclusive, <= roundup16(nbv) <= NB
+
+                // factor tables of K_s: (u^2, 1-u^2) per x and (v^2, 1-v^2) per y
 #pragma unroll
-                    for (int kg = 0; kg < 2; ++kg) {
-                        uint32_t bh[4], bl[4];
+                for (int i = 0; i < 8; ++i) {
+                    const int qq = i * 32 + lane, x = qq >> 4, k = qq & 15;
+                    const float ex = __shfl_sync(0xffffffffu, e.x, k);
+                    const float du = ((float)(X0 + x) + 0.5f - ex) * pl.inv_hs;
+                    const float u2 = du * du;
+                    ptx::sts_f2(tabx + x * TAB_ROW + k * 8, make_float2(u2, 1.0f - u2));
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int qq = i * 32 + lane, y = qq >> 4, k = qq & 15;
+                    const float ey = __shfl_sync(0xffffffffu, e.y, k);
+                    const float dv = ((float)(Y0 + y) + 0.5f - ey) * pl.inv_hs;
+                    const float v2 = dv * dv;
+                    ptx::sts_f2(taby + y * TAB_ROW + k * 8, make_float2(v2, 1.0f - v2));
+                }
+                if (lane < CHUNK) ptx::sts_f(tt + lane * 4, e.z);
+                __syncwarp();
+
+                if (!(ok = wait_warp(c, bar(L::sempty(gi)), (suse & 1u) ^ 1u))) break;
+                // A = K_s without c_s: row r = voxel (x = r / 8, y = r % 8); lane owns
+                // rows lane + 32 j, all with y = lane % 8
+#pragma unroll
+                for (int kg = 0; kg < 2; ++kg) {
+                    float4 fy[4];
+#pragma unroll
+                    for (int kp = 0; kp < 4; ++kp)
+                        fy[kp] = ptx::lds_f4(taby + (lane & 7) * TAB_ROW + (kg * 8 + 2 * kp) * 8);
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int r = lane + 32 * jj;
+                        uint32_t ah[4], al[4];
 #pragma unroll
                         for (int kp = 0; kp < 4; ++kp) {
-                            const float w0 = (tc - tk[kg * 8 + 2 * kp]) * pl.inv_ht;
-                            const float w1 = (tc - tk[kg * 8 + 2 * kp + 1]) * pl.inv_ht;
-                            const float b0 = csct * fmaxf(fmaf(-w0, w0, 1.0f), 0.0f);
-                            const float b1 = csct * fmaxf(fmaf(-w1, w1, 1.0f), 0.0f);
-                            split2<FP16>(b0, b1, bh[kp], bl[kp]);
+                            const float4 fx = ptx::lds_f4(tabx + (r >> 3) * TAB_ROW + (kg * 8 + 2 * kp) * 8);
+                            const float a0 = (fx.x + fy[kp].x < 1.0f) ? fx.y * fy[kp].y : 0.0f;
+                            const float a1 = (fx.z + fy[kp].z < 1.0f) ? fx.w * fy[kp].w : 0.0f;
+                            split2<FP16>(a0, a1, ah[kp], al[kp]);
                         }
-                        const uint32_t off = (uint32_t)(n >> 3) * CORE_SBO + kg * CORE_LBO + (n & 7) * 16;
-                        ptx::sts_u4(b_hi + off, bh[0], bh[1], bh[2], bh[3]);
-                        ptx::sts_u4(b_lo + off, bl[0], bl[1], bl[2], bl[3]);
+                        const uint32_t off = (uint32_t)(r >> 3) * CORE_SBO + kg * CORE_LBO + (r & 7) * 16;
+                        ptx::sts_u4(a_hi + off, ah[0], ah[1], ah[2], ah[3]);
+                        ptx::sts_u4(a_lo + off, al[0], al[1], al[2], al[3]);
                     }
                 }
-                const int more = (cw + NCAP < cend) ? F_MORE : 0;
-                if (lane == 0) ptx::sts_i4(shdr, make_int4(cw, ncols, F_CHUNK | more, 0));
-                ptx::fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(bar(L::sfull(gw)));
-                ++suse;
+                // B = c_s c_t (1 - w^2)_+ in column windows of up to NCAP
+                float tk[CHUNK];
+#pragma unroll
+                for (int k4 = 0; k4 < CHUNK / 4; ++k4) {
+                    const float4 t4 = ptx::lds_f4(tt + k4 * 16);
+                    tk[4 * k4] = t4.x; tk[4 * k4 + 1] = t4.y; tk[4 * k4 + 2] = t4.z; tk[4 * k4 + 3] = t4.w;
+                }
+                for (int cw = c0; cw < cend && ok; cw += NCAP) {
+                    if (cw != c0 && !(ok = wait_warp(c, bar(L::sempty(gi)), (suse & 1u) ^ 1u))) break;
+                    const int ncols = min(NCAP, cend - cw);
+                    for (int n = lane; n < ncols; n += 32) {
+                        const float tc = (float)(T0 + cw + n) + 0.5f;
+#pragma unroll
+                        for (int kg = 0; kg < 2; ++kg) {
+                            uint32_t bh[4], bl[4];
+#pragma unroll
+                            for (int kp = 0; kp < 4; ++kp) {
+                                const float w0 = (tc - tk[kg * 8 + 2 * kp]) * pl.inv_ht;
+                                const float w1 = (tc - tk[kg * 8 + 2 * kp + 1]) * pl.inv_ht;
+                                const float b0 = csct * fmaxf(fmaf(-w0, w0, 1.0f), 0.0f);
+                                const float b1 = csct * fmaxf(fmaf(-w1, w1, 1.0f), 0.0f);
+                                split2<FP16>(b0, b1, bh[kp], bl[kp]);
+                            }
+                            const uint32_t off = (uint32_t)(n >> 3) * CORE_SBO + kg * CORE_LBO + (n & 7) * 16;
+                            ptx::sts_u4(b_hi + off, bh[0], bh[1], bh[2], bh[3]);
+                            ptx::sts_u4(b_lo + off, bl[0], bl[1], bl[2], bl[3]);
+                        }
+                    }
+                    const bool more = cw + NCAP < cend;
+                    const int fl = F_MMA | (more ? F_MORE : 0) |
+                                   ((!more && ch == nch - 1) ? (F_PAGE_END | end) : 0);
+                    publish(cw, ncols, fl);
+                }
             }
+            if (!ok) break;
+            // done with the page: order these generic accesses before the loader's
+            // next bulk copy into it, then release it
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(bar(L::pempty(p)));
         }
     } else if (warp == WARP_MMA) {
         // --------------------------------------------------------------- MMA
         if (lane == 0) {
             uint32_t par = 0;  // bit g: parity of the next use of generator g's stage
             uint32_t seg = 0;  // accumulator segments opened so far
-            uint32_t jm = 0;   // next chunk slot
+            uint32_t qm = 0;   // next page
             bool ok = true;
             const uint32_t fmt = FP16 ? 0u : 1u;
+            // descriptors of stage 0; stage g adds g * STAGE_BYTES / 16 to the address field
+            const uint64_t d_ahi = ptx::smem_desc(sb + L::OFF_STAGE, CORE_LBO, CORE_SBO);
+            const uint64_t d_alo = d_ahi + (A_BYTES >> 4);
+            const uint64_t d_bhi = d_ahi + ((2 * A_BYTES) >> 4);
+            const uint64_t d_blo = d_ahi + ((2 * A_BYTES + B_BYTES) >> 4);
+            // chunks per 32-column block before a segment is closed, four blocks per word
+            const uint32_t thr4 = (uint32_t)flush_chunks * 0x01010101u;
             for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 int b = (int)(seg & 1u);
                 if (!(ok = wait_bar(c, bar(L::aempty(b)), (seg >> 1) & 1u))) break;
                 ptx::tc_fence_after();
                 int first = 1;
-                uint32_t touched = 0;            // 32-column blocks written in this segment
-                uint16_t steps[NB / 16];         // accumulation steps per 16-column block
-#pragma unroll
-                for (int q = 0; q < NB / 16; ++q) steps[q] = 0;
-                bool done = false;
-                while (!done && ok) {
-                    const int gq = (int)(jm % NGEN);
-                    bool more = true;
-                    while (more && ok) {
-                        if (!(ok = wait_bar(c, bar(L::sfull(gq)), (par >> gq) & 1u))) break;
-                        par ^= 1u << gq;
-                        ptx::tc_fence_after();
-                        const int4 h = ptx::lds_i4(sb + L::OFF_SHDR + gq * 16);
-                        more = (h.z & F_MORE) != 0;
-                        if (h.z & F_END) {
-                            ptx::mbar_arrive(bar(L::sempty(gq)));
-                            done = true;
-                            break;
+                uint32_t touched = 0;             // 32-column blocks written in this segment
+                uint32_t cnt_lo = 0, cnt_hi = 0;  // chunks per 32-column block (bytes)
+                int flags = 0;
+                while (!(flags & F_ITEM_END) && ok) {
+                    flags = 0;
+                    for (uint32_t ch = 0; !(flags & F_PAGE_END) && ok; ++ch) {
+                        const int gq = (int)((qm + ch) % NGEN);
+                        flags = F_MORE;
+                        while ((flags & F_MORE) && ok) {
+                            if (!(ok = wait_bar(c, bar(L::sfull(gq)), (par >> gq) & 1u))) break;
+                            par ^= 1u << gq;
+                            const int4 h = ptx::lds_i4(sb + L::OFF_SHDR + gq * 16);
+                            flags = h.z;
+                            if (!(flags & F_MMA)) {
+                                ptx::mbar_arrive(bar(L::sempty(gq)));
+                                continue;
+                            }
+                            const bool in_range = h.x >= 0 && h.y >= 16 && h.y <= NCAP &&
+                                                  (h.y & 15) == 0 && h.x + h.y <= NB && (h.x & 15) == 0;
+                            if (!in_range) {  // never issue an MMA outside the accumulator
+                                atomicOr(err, ERRBIT_BOUNDS);
+                                ptx::mbar_arrive(bar(L::sempty(gq)));
+                                continue;
+                            }
+                            const uint32_t b0 = (uint32_t)h.x >> 5, b1 = (uint32_t)(h.x + h.y - 1) >> 5;
+                            const uint32_t mask = ((2u << b1) - 1u) & ~((1u << b0) - 1u);
+                            const uint32_t inc_lo = ((mask & 15u) * 0x204081u) & 0x01010101u;
+                            const uint32_t inc_hi = ((mask >> 4) * 0x204081u) & 0x01010101u;
+                            uint32_t n_lo = cnt_lo + inc_lo, n_hi = cnt_hi + inc_hi;
+                            if (__vcmpgtu4(n_lo, thr4) | __vcmpgtu4(n_hi, thr4)) {
+                                // close the segment: the epilogue adds it in fp32
+                                ptx::sts_i4(sb + L::OFF_DESC + b * 16,
+                                            make_int4((int)(item & 0xffffffff), (int)(item >> 32), first, (int)touched));
+                                ptx::mbar_arrive(bar(L::dfull(b)));
+                                ptx::tc_commit(bar(L::afull(b)));
+                                ++seg;
+                                b = (int)(seg & 1u);
+                                if (!(ok = wait_bar(c, bar(L::aempty(b)), (seg >> 1) & 1u))) break;
+                                ptx::tc_fence_after();
+                                first = 0;
+                                touched = 0;
+                                n_lo = inc_lo;
+                                n_hi = inc_hi;
+                            }
+                            cnt_lo = n_lo;
+                            cnt_hi = n_hi;
+                            touched |= mask;
+                            const uint64_t so = (uint64_t)gq * (STAGE_BYTES >> 4);
+                            const uint32_t idesc = ptx::idesc_f16(128, (uint32_t)h.y, fmt);
+                            const uint32_t d = tmem + (uint32_t)(b * NB + h.x);
+                            ptx::mma_f16_ss(d, d_ahi + so, d_bhi + so, idesc, 1);
+                            ptx::mma_f16_ss(d, d_ahi + so, d_blo + so, idesc, 1);
+                            ptx::mma_f16_ss(d, d_alo + so, d_bhi + so, idesc, 1);
+                            ptx::tc_commit(bar(L::sempty(gq)));
                         }
-                        const bool in_range = h.x >= 0 && h.y >= 16 && h.y <= NCAP &&
-                                              (h.y & 15) == 0 && h.x + h.y <= NB && (h.x & 15) == 0;
-                        if (!in_range) {  // never issue an MMA outside the accumulator
-                            atomicOr(err, ERRBIT_BOUNDS);
-                            ptx::mbar_arrive(bar(L::sempty(gq)));
-                            continue;
-                        }
-                        const int blo = h.x >> 4, bhi = (h.x + h.y) >> 4;
-                        bool full = false;
-#pragma unroll
-                        for (int q = 0; q < NB / 16; ++q)
-                            if (q >= blo && q < bhi && steps[q] + 3 > flush_steps) full = true;
-                        if (full) {
-                            // close the segment: the epilogue adds it in fp32
-                            ptx::sts_i4(sb + L::OFF_DESC + b * 16,
-                                        make_int4((int)(item & 0xffffffff), (int)(item >> 32), first, (int)touched));
-                            ptx::mbar_arrive(bar(L::dfull(b)));
-                            ptx::tc_commit(bar(L::afull(b)));
-                            ++seg;
-                            b = (int)(seg & 1u);
-                            if (!(ok = wait_bar(c, bar(L::aempty(b)), (seg >> 1) & 1u))) break;
-                            ptx::tc_fence_after();
-                            first = 0;
-                            touched = 0;
-#pragma unroll
-                            for (int q = 0; q < NB / 16; ++q) steps[q] = 0;
-                        }
-#pragma unroll
-                        for (int q = 0; q < NB / 16; ++q)
-                            if (q >= blo && q < bhi) steps[q] += 3;
-                        for (int q = h.x >> 5; q <= (h.x + h.y - 1) >> 5; ++q) touched |= 1u << q;
-                        const uint32_t st = sb + L::OFF_STAGE + (uint32_t)gq * STAGE_BYTES;
-                        const uint64_t ahi = ptx::smem_desc(st, CORE_LBO, CORE_SBO);
-                        const uint64_t alo = ptx::smem_desc(st + A_BYTES, CORE_LBO, CORE_SBO);
-                        const uint64_t bhi_d = ptx::smem_desc(st + 2 * A_BYTES, CORE_LBO, CORE_SBO);
-                        const uint64_t blo_d = ptx::smem_desc(st + 2 * A_BYTES + B_BYTES, CORE_LBO, CORE_SBO);
-                        const uint32_t idesc = ptx::idesc_f16(128, (uint32_t)h.y, fmt);
-                        const uint32_t d = tmem + (uint32_t)(b * NB + h.x);
-                        ptx::mma_f16_ss(d, ahi, bhi_d, idesc, 1);
-                        ptx::mma_f16_ss(d, ahi, blo_d, idesc, 1);
-                        ptx::mma_f16_ss(d, alo, bhi_d, idesc, 1);
-                        ptx::tc_commit(bar(L::sempty(gq)));
                     }
-                    ++jm;
+                    ++qm;
                 }
                 if (!ok) break;
                 ptx::sts_i4(sb + L::OFF_DESC + b * 16,
@@ -583,7 +560,7 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             drain_bar(bar(L::drain()), 0);
         }
         __syncwarp();
-    } else {
+    } else if (warp >= WARP_EPI0) {
         // ---------------------------------------------------------- epilogue
         const int q = warp & 3;
         const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
@@ -683,10 +660,11 @@ bool launch_cfg(const Plan& pl, const Bins& b, float* out, int* err, cudaStream_
     const int64_t items = (int64_t)pl.ntx * pl.nty * ntb;
     if (items <= 0) return true;
     const int grid = (int)(items < sms ? items : sms);
-    // accumulation steps per 16-column block before a segment is closed: bounds
-    // the round-toward-zero drift of the tensor-core accumulation per segment
-    const int flush_steps = FP16 ? 192 : 384;
-    kern<<<grid, NTHREADS, L::TOTAL, st>>>(pl, b.ev, b.start, out, err, items, flush_steps);
+    // chunks (three accumulation steps each) per 32-column block before a segment
+    // is closed: bounds the round-toward-zero drift of the tensor-core
+    // accumulation per segment
+    const int flush_chunks = FP16 ? 64 : 128;
+    kern<<<grid, NTHREADS, L::TOTAL, st>>>(pl, b.ev, b.start, out, err, items, flush_chunks);
     return true;
 }
 
