@@ -97,7 +97,7 @@ struct L {
     static constexpr uint32_t OFF_PAGES = OFF_STAGE + NGEN * STAGE_BYTES;
     static constexpr uint32_t OFF_TAB = OFF_PAGES + NPAGES * PAGE * 16;
     static constexpr uint32_t OFF_SHDR = OFF_TAB + NGEN * TAB_BYTES;
-    static constexpr uint32_t OFF_PMETA = OFF_SHDR + NGEN * 16;
+    static constexpr uint32_t OFF_PMETA = OFF_SHDR + NGEN * 32;
     static constexpr uint32_t OFF_KEPT = OFF_PMETA + NPAGES * 16;
     static constexpr uint32_t OFF_DESC = OFF_KEPT + NPAGES * 16;
     static constexpr uint32_t OFF_BAR = OFF_DESC + NACC * 16;
@@ -306,18 +306,76 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
         const uint32_t stg = sb + L::OFF_STAGE + gi * STAGE_BYTES;
         const uint32_t a_hi = stg, a_lo = stg + A_BYTES, b_hi = stg + 2 * A_BYTES,
                        b_lo = b_hi + B_BYTES;
-        const uint32_t shdr = sb + L::OFF_SHDR + gi * 16;
+        const uint32_t shdr = sb + L::OFF_SHDR + gi * 32;
         const uint32_t lt = (1u << lane) - 1u;
         const float csct = pl.cs * pl.ct;
         uint32_t suse = 0;  // uses of this warp's stage
         bool ok = true;
-        // hands the stage to the MMA thread
+        // hands the stage to the MMA thread, with what it needs precomputed: the
+        // instruction descriptor, the 32-column blocks the MMAs touch and the
+        // per-block chunk-count increments (bytes, four blocks per word)
+        const uint32_t fmt = FP16 ? 0u : 1u;
         auto publish = [&](int c0, int ncols, int flags) {
-            if (lane == 0) ptx::sts_i4(shdr, make_int4(c0, ncols, flags, 0));
+            if (lane == 0) {
+                uint32_t idesc = 0, mask = 0, inc_lo = 0, inc_hi = 0;
+                if (flags & F_MMA) {
+                    idesc = ptx::idesc_f16(128, (uint32_t)ncols, fmt);
+                    const uint32_t b0 = (uint32_t)c0 >> 5, b1 = (uint32_t)(c0 + ncols - 1) >> 5;
+                    mask = ((2u << b1) - 1u) & ~((1u << b0) - 1u);
+                    inc_lo = ((mask & 15u) * 0x204081u) & 0x01010101u;
+                    inc_hi = ((mask >> 4) * 0x204081u) & 0x01010101u;
+                }
+                ptx::sts_i4(shdr, make_int4(c0, ncols, flags, 0));
+                ptx::sts_i4(shdr + 16, make_int4((int)idesc, (int)mask, (int)inc_lo, (int)inc_hi));
+            }
             ptx::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(bar(L::sfull(gi)));
             ++suse;
+        };
+        // Keeps the events of page fq (staged, owned by this generator) whose
+        // cylinder reaches their tile, compacted in place, and publishes the count.
+        uint32_t filt_next = (uint32_t)gi;  // next owned page not yet filtered
+        auto filter_page = [&](uint32_t fq) {
+            const uint32_t fp = fq % NPAGES;
+            const uint32_t fb = sb + L::OFF_PAGES + fp * PAGE * 16;
+            const int4 fm = ptx::lds_i4(sb + L::OFF_PMETA + fp * 16);
+            uint32_t kept = 0;
+            if (!(fm.y & F_TERM)) {
+                const int64_t fitem = (int64_t)(uint32_t)fm.z | ((int64_t)fm.w << 32);
+                int ftx, fty, ftb;
+                decode_item(pl, fitem, ftx, fty, ftb);
+                const TileGeom fg = tile_geom(pl, ftx, fty, ftb, NB);
+                for (int r = 0; r * 32 < fm.x; ++r) {
+                    const int slot = r * 32 + lane;
+                    float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+                    bool keep = false;
+                    if (slot < fm.x) {
+                        e = ptx::lds_f4(fb + slot * 16u);
+                        keep = reaches(pl, fg, e);
+                    }
+                    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+                    __syncwarp();
+                    if (keep) ptx::sts_f4(fb + (kept + __popc(bal & lt)) * 16u, e);
+                    kept += __popc(bal);
+                    __syncwarp();
+                }
+            }
+            if (lane == 0) {
+                ptx::sts_i4(sb + L::OFF_KEPT + fp * 16, make_int4((int)kept, 0, 0, 0));
+                ptx::mbar_arrive(bar(L::pfilt(fp)));
+            }
+            __syncwarp();
+            filt_next = fq + NGEN;
+        };
+        // filters the next owned page ahead of time if it is already staged
+        auto filter_ahead = [&](uint32_t q) {
+            if (filt_next > q && filt_next < q + NPAGES) {
+                const uint32_t fp = filt_next % NPAGES;
+                const bool ready = __all_sync(0xffffffffu,
+                    ptx::mbar_try_wait(bar(L::pfull(fp)), (filt_next / NPAGES) & 1u));
+                if (ready) filter_page(filt_next);
+            }
         };
         for (uint32_t q = 0; ok; ++q) {
             const uint32_t p = q % NPAGES;
@@ -332,39 +390,20 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             decode_item(pl, item, tx, ty, tb);
             const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
             const int X0 = g.X0, Y0 = g.Y0, T0 = g.T0, nbv = g.T1 - g.T0;
-            const int own = (int)(q % NGEN) == gi;
-            if (own) {
-                // keep the events whose cylinder reaches the tile, compacted in place
-                uint32_t kept = 0;
-                for (int r = 0; r * 32 < meta.x; ++r) {
-                    const int slot = r * 32 + lane;
-                    float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-                    bool keep = false;
-                    if (slot < meta.x) {
-                        e = ptx::lds_f4(pgb + slot * 16u);
-                        keep = reaches(pl, g, e);
-                    }
-                    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-                    __syncwarp();
-                    if (keep) ptx::sts_f4(pgb + (kept + __popc(bal & lt)) * 16u, e);
-                    kept += __popc(bal);
-                    __syncwarp();
-                }
-                if (lane == 0) {
-                    ptx::sts_i4(sb + L::OFF_KEPT + p * 16, make_int4((int)kept, 0, 0, 0));
-                    ptx::mbar_arrive(bar(L::pfilt(p)));
-                }
-                __syncwarp();
+            if ((int)(q % NGEN) == gi && q >= filt_next) {
+                // this generator owns page q and has not filtered it ahead: do it now
+                filter_page(q);
             } else if (!(ok = wait_warp(c, bar(L::pfilt(p)), ph))) {
                 break;
             }
             const int kept = ptx::lds_i4(sb + L::OFF_KEPT + p * 16).x;
             const int nch = (kept + CHUNK - 1) / CHUNK;
-            if (nch == 0 && own) {  // nothing to add: just mark the page's end
+            if (nch == 0 && (int)(q % NGEN) == gi) {  // nothing to add: just mark the page's end
                 if (!(ok = wait_warp(c, bar(L::sempty(gi)), (suse & 1u) ^ 1u))) break;
                 publish(0, 0, F_PAGE_END | end);
             }
             for (int ch = (int)((gi - (int)(q % NGEN) + NGEN) % NGEN); ch < nch && ok; ch += NGEN) {
+                filter_ahead(q);
                 const int count = min(CHUNK, kept - ch * CHUNK);
                 float4 e = make_float4(1.0e30f, 1.0e30f, 1.0e30f, 0.f);
                 if (lane < count) e = ptx::lds_f4(pgb + (ch * CHUNK + lane) * 16u);
@@ -477,7 +516,6 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             uint32_t seg = 0;  // accumulator segments opened so far
             uint32_t qm = 0;   // next page
             bool ok = true;
-            const uint32_t fmt = FP16 ? 0u : 1u;
             // descriptors of stage 0; stage g adds g * STAGE_BYTES / 16 to the address field
             const uint64_t d_ahi = ptx::smem_desc(sb + L::OFF_STAGE, CORE_LBO, CORE_SBO);
             const uint64_t d_alo = d_ahi + (A_BYTES >> 4);
@@ -501,23 +539,20 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                         while ((flags & F_MORE) && ok) {
                             if (!(ok = wait_bar(c, bar(L::sfull(gq)), (par >> gq) & 1u))) break;
                             par ^= 1u << gq;
-                            const int4 h = ptx::lds_i4(sb + L::OFF_SHDR + gq * 16);
+                            const int4 h = ptx::lds_i4(sb + L::OFF_SHDR + gq * 32);
+                            const int4 h1 = ptx::lds_i4(sb + L::OFF_SHDR + gq * 32 + 16);
                             flags = h.z;
-                            if (!(flags & F_MMA)) {
+                            // never issue an MMA outside the accumulator
+                            const bool in_range = (uint32_t)h.x + (uint32_t)h.y <= (uint32_t)NB &&
+                                                  (uint32_t)(h.y - 16) <= (uint32_t)(NCAP - 16) &&
+                                                  ((h.x | h.y) & 15) == 0;
+                            if (!(flags & F_MMA) || !in_range) {
+                                if ((flags & F_MMA) && !in_range) atomicOr(err, ERRBIT_BOUNDS);
                                 ptx::mbar_arrive(bar(L::sempty(gq)));
                                 continue;
                             }
-                            const bool in_range = h.x >= 0 && h.y >= 16 && h.y <= NCAP &&
-                                                  (h.y & 15) == 0 && h.x + h.y <= NB && (h.x & 15) == 0;
-                            if (!in_range) {  // never issue an MMA outside the accumulator
-                                atomicOr(err, ERRBIT_BOUNDS);
-                                ptx::mbar_arrive(bar(L::sempty(gq)));
-                                continue;
-                            }
-                            const uint32_t b0 = (uint32_t)h.x >> 5, b1 = (uint32_t)(h.x + h.y - 1) >> 5;
-                            const uint32_t mask = ((2u << b1) - 1u) & ~((1u << b0) - 1u);
-                            const uint32_t inc_lo = ((mask & 15u) * 0x204081u) & 0x01010101u;
-                            const uint32_t inc_hi = ((mask >> 4) * 0x204081u) & 0x01010101u;
+                            const uint32_t mask = (uint32_t)h1.y;
+                            const uint32_t inc_lo = (uint32_t)h1.z, inc_hi = (uint32_t)h1.w;
                             uint32_t n_lo = cnt_lo + inc_lo, n_hi = cnt_hi + inc_hi;
                             if (__vcmpgtu4(n_lo, thr4) | __vcmpgtu4(n_hi, thr4)) {
                                 // close the segment: the epilogue adds it in fp32
@@ -538,7 +573,7 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                             cnt_hi = n_hi;
                             touched |= mask;
                             const uint64_t so = (uint64_t)gq * (STAGE_BYTES >> 4);
-                            const uint32_t idesc = ptx::idesc_f16(128, (uint32_t)h.y, fmt);
+                            const uint32_t idesc = (uint32_t)h1.x;
                             const uint32_t d = tmem + (uint32_t)(b * NB + h.x);
                             ptx::mma_f16_ss(d, d_ahi + so, d_bhi + so, idesc, 1);
                             ptx::mma_f16_ss(d, d_ahi + so, d_blo + so, idesc, 1);
@@ -602,18 +637,22 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                 if (!valid) continue;
                 const int nv = min(32, nbv - col);
                 if (vec && nv == 32) {
+                    float4* p4 = reinterpret_cast<float4*>(dst + col);
+                    float4 pv[8];
+                    if (!first) {  // earlier segments of this tile: load all, then add
+#pragma unroll
+                        for (int v4 = 0; v4 < 8; ++v4) pv[v4] = p4[v4];
+                    }
 #pragma unroll
                     for (int v4 = 0; v4 < 8; ++v4) {
                         float4 o = make_float4(__uint_as_float(r[4 * v4]) * pl.norm,
                                                __uint_as_float(r[4 * v4 + 1]) * pl.norm,
                                                __uint_as_float(r[4 * v4 + 2]) * pl.norm,
                                                __uint_as_float(r[4 * v4 + 3]) * pl.norm);
-                        float4* p4 = reinterpret_cast<float4*>(dst + col) + v4;
                         if (!first) {
-                            const float4 pv = *p4;
-                            o.x += pv.x; o.y += pv.y; o.z += pv.z; o.w += pv.w;
+                            o.x += pv[v4].x; o.y += pv[v4].y; o.z += pv[v4].z; o.w += pv[v4].w;
                         }
-                        if (last) __stcs(p4, o); else *p4 = o;
+                        if (last) __stcs(p4 + v4, o); else p4[v4] = o;
                     }
                 } else {
 #pragma unroll
