@@ -155,6 +155,37 @@ STKDE_API int stkde_phase_times(stkde_ctx* ctx, float* ms, int cap);
 /* Number of library kernels the last stkde_compute enqueued (0 for a NULL ctx). */
 STKDE_API int stkde_last_launch_count(stkde_ctx* ctx);
 
+/* Largest problem stkde_compute_static accepts: events, and bin boundaries
+ * (number of event bins + 1; a bin is 16 x 8 voxels in the plane by a slab of
+ * 4 voxels of T, so roughly gx*gy*gt/512 bins). */
+#define STKDE_STATIC_MAX_EVENTS 262144
+#define STKDE_STATIC_MAX_BINS 1048576
+
+/* stkde_compute without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code where
+ * another component owns every device allocation (a host application's or a
+ * framework's memory pool, an arena reserved up front), or a loop that must not
+ * take the device-wide synchronisation of cudaMalloc/cudaFree.  It needs no
+ * context: `points` (n x 3 doubles) and `out` (gx*gy*gt binary32) must be
+ * device memory of the current device, the work is ordered on `stream`
+ * (cudaStream_t, NULL = legacy default stream), `form` and `kernel_constants`
+ * are as in stkde_options.  All scratch lives in one fixed file-scope device
+ * array of about 16 MB that every device loading the library keeps until the
+ * process exits; its device address is looked up once per device on the first
+ * call made with that device current, so make that first call before any
+ * stream capture.  All calls on a device share that array: calls whose work
+ * overlaps on the GPU race and must be serialised by the caller.
+ * Returns STKDE_ERR_UNSUPPORTED, before any launch, when n exceeds
+ * STKDE_STATIC_MAX_EVENTS or the grid needs more than STKDE_STATIC_MAX_BINS bin
+ * boundaries; INVALID_ARGUMENT for host pointers or the argument errors of
+ * stkde_compute.  With sync != 0 the call waits for the stream and returns
+ * device-side errors (non-finite coordinates, timeouts); with sync == 0 it
+ * returns after enqueueing and device-side errors are not reported. */
+STKDE_API stkde_status stkde_compute_static(const double* points, int64_t n,
+                                            const stkde_grid* grid, double hs, double ht,
+                                            float* out, int form, int kernel_constants,
+                                            void* stream, int sync);
+
 /* Frees the context and its workspace (waits for its stream first). */
 STKDE_API void stkde_destroy(stkde_ctx* ctx);
 

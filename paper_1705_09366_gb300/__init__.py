@@ -18,7 +18,7 @@ __all__ = [
     "Options", "Grid", "Problem", "StkdeError", "Context", "lib", "lib_path",
     "stkde_default_options", "stkde_create", "stkde_compute", "stkde_compute_batch",
     "stkde_count_updates", "stkde_synchronize", "stkde_phase_times", "stkde_destroy",
-    "stkde_status_string", "stkde_last_launch_count", "FORM_TENSOR_BF16X3", "FORM_TENSOR_FP16X3", "FORM_FP32",
+    "stkde_status_string", "stkde_last_launch_count", "stkde_compute_static", "FORM_TENSOR_BF16X3", "FORM_TENSOR_FP16X3", "FORM_FP32",
     "FORM_SCATTER", "KERNEL_PRINTED", "KERNEL_UNIT_MASS", "EXPORTED_SYMBOLS",
 ]
 
@@ -46,8 +46,11 @@ KERNEL_UNIT_MASS = 1
 EXPORTED_SYMBOLS = (
     "stkde_default_options", "stkde_create", "stkde_compute", "stkde_compute_batch",
     "stkde_count_updates", "stkde_synchronize", "stkde_phase_times", "stkde_destroy",
-    "stkde_status_string", "stkde_last_launch_count",
+    "stkde_status_string", "stkde_last_launch_count", "stkde_compute_static",
 )
+
+STATIC_MAX_EVENTS = 262144
+STATIC_MAX_BINS = 1048576
 
 
 class Options(ctypes.Structure):
@@ -100,6 +103,9 @@ def lib():
         l.stkde_synchronize.restype = ctypes.c_int
         l.stkde_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
         l.stkde_phase_times.restype = ctypes.c_int
+        l.stkde_compute_static.argtypes = [vp, i64, ctypes.POINTER(Grid), dbl, dbl, vp, ctypes.c_int,
+                                           ctypes.c_int, vp, ctypes.c_int]
+        l.stkde_compute_static.restype = ctypes.c_int
         l.stkde_last_launch_count.argtypes = [vp]
         l.stkde_last_launch_count.restype = ctypes.c_int
         l.stkde_destroy.argtypes = [vp]
@@ -194,6 +200,16 @@ def stkde_phase_times(ctx, cap: int = 8) -> list[float]:
     buf = (ctypes.c_float * cap)()
     k = lib().stkde_phase_times(ctx, buf, cap)
     return [float(buf[i]) for i in range(k)]
+
+
+def stkde_compute_static(points, n: int, grid: Grid, hs: float, ht: float, out, form="bf16x3",
+                         kernel_constants: int = 0, stream=None, sync: bool = True) -> None:
+    """Allocation-free density (see include/stkde.h): `points` and `out` are
+    device buffers of the current device; scratch is a fixed library-owned array."""
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    _check(lib().stkde_compute_static(_ptr(points), int(n), ctypes.byref(grid), float(hs), float(ht),
+                                      _ptr(out), f, int(kernel_constants), _stream_handle(stream),
+                                      int(bool(sync))), "stkde_compute_static")
 
 
 def stkde_last_launch_count(ctx) -> int:

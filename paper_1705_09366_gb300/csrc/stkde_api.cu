@@ -92,7 +92,7 @@ stkde_status check_problem(const double* points, int64_t n, const stkde_grid* g,
     return STKDE_OK;
 }
 
-Plan make_plan(const stkde_ctx* c, int64_t n, const stkde_grid* g, double hs, double ht,
+Plan make_plan(int kernel_constants, int64_t n, const stkde_grid* g, double hs, double ht,
                int slab_opt) {
     Plan p{};
     p.gx = (int)g->gx; p.gy = (int)g->gy; p.gt = (int)g->gt;
@@ -101,7 +101,7 @@ Plan make_plan(const stkde_ctx* c, int64_t n, const stkde_grid* g, double hs, do
     p.inv_hs = (float)(g->sres / hs);
     p.inv_ht = (float)(g->tres / ht);
     const double pi = 3.14159265358979323846;
-    p.cs = (float)(c->opt.kernel_constants == STKDE_KERNEL_UNIT_MASS ? 24.0 / (13.0 * pi) : pi / 2.0);
+    p.cs = (float)(kernel_constants == STKDE_KERNEL_UNIT_MASS ? 24.0 / (13.0 * pi) : pi / 2.0);
     p.ct = 0.75f;
     p.norm = n > 0 ? (float)(1.0 / ((double)n * hs * hs * ht)) : 0.0f;
     p.ntx = (p.gx + TX - 1) / TX;
@@ -200,6 +200,16 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
 }
 
 }  // namespace
+
+namespace stkde {
+stkde_status check_problem_args(const double* points, int64_t n, const stkde_grid* g, double hs,
+                                double ht) {
+    return check_problem(points, n, g, hs, ht);
+}
+Plan plan_problem(int kernel_constants, int64_t n, const stkde_grid* g, double hs, double ht) {
+    return make_plan(kernel_constants, n, g, hs, ht, 0);
+}
+}  // namespace stkde
 
 extern "C" {
 
@@ -328,7 +338,7 @@ stkde_status stkde_compute(stkde_ctx* c, const double* points, int64_t n, const 
         }
         const int pkind = pointer_kind(points, c->device);
         if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
-        const Plan pl = make_plan(c, n, g, hs, ht, c->opt.slab);
+        const Plan pl = make_plan(c->opt.kernel_constants, n, g, hs, ht, c->opt.slab);
         Workspace w;
         const size_t need = carve(nullptr, (int)n, pl.nkeys, pkind == 0, nullptr);
         s = ensure_ws(c, need);
@@ -366,7 +376,7 @@ stkde_status stkde_count_updates(stkde_ctx* c, const double* points, int64_t n,
     if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
     const int pkind = pointer_kind(points, c->device);
     if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
-    const Plan pl = make_plan(c, n, g, hs, ht, c->opt.slab);
+    const Plan pl = make_plan(c->opt.kernel_constants, n, g, hs, ht, c->opt.slab);
     Workspace w;
     s = ensure_ws(c, carve(nullptr, (int)n, pl.nkeys, pkind == 0, nullptr));
     if (s != STKDE_OK) return s;
