@@ -10,37 +10,41 @@
 // instruction, N = the T columns the 16 events' windows cover, the fp32
 // accumulator in tensor memory.  For accuracy A and B are split into a 16-bit
 // high part and a 16-bit remainder and three products hi*hi + hi*lo + lo*hi are
-// accumulated (the dropped lo*lo term is below 2^-16 relative).
+// accumulated (the dropped lo*lo term is below 2^-15 relative).
 //
 // The tensor cores round each accumulation step toward zero, so a long run of
-// steps into one accumulator drifts low.  The MMA thread therefore closes an
+// steps into one accumulator drifts low.  The MMA warp therefore closes an
 // accumulator "segment" before any 32-column block of it has taken more than a
 // fixed number of chunks; the epilogue stores the first segment of a tile and
 // adds later ones to it in fp32 (round to nearest), which bounds the drift.
 //
 // Persistent CTA per SM, warp-specialised, every hand-off through mbarriers
-// (warp w runs on scheduler w % 4; the MMA thread shares its scheduler only
-// with the light loader and one epilogue warp):
-//   warp 0            MMA issue (one thread), tensor-memory allocation
-//   warp 4            loader: walks the tile's event bins and stages them, in
-//                     bin order, into 256-event shared-memory pages with
-//                     cp.async.bulk (no multicast), one copy per bin run, all
-//                     lanes issuing in parallel
-//   warps 1-3,5-7,9,10  generators: every generator reads every page; the
-//                     page's owner (page q: generator q mod 8) keeps the events
-//                     whose cylinder reaches the tile, compacting the page in
-//                     place, and chunk c of the page -- kept events 16c..16c+15
-//                     -- is built by generator (q + c) mod 8 in its own operand
-//                     stage: A = K_s and B = K_t as hi and lo 16-bit tiles (B in
-//                     column windows of up to 128)
-//   warps 12-15       epilogue: one per tensor-memory lane quarter; scales by
-//                     1/(n hs^2 ht), writes each voxel of the tile (vector
-//                     stores), adds later segments, zeroes the accumulator
+// (warp w runs on scheduler w % 4; the MMA warp shares its scheduler only with
+// the light loader and one epilogue warp):
+//   warp 0             MMA issue (the whole warp runs the loop, one elected
+//                      lane issues), tensor-memory allocation
+//   warp 4             loader: walks the tile's event bins and stages them, in
+//                      bin order, into 256-event shared-memory pages with
+//                      cp.async.bulk (no multicast), one copy per bin run, all
+//                      lanes issuing in parallel
+//   warps 1-3,5-7,9-11 nine generators.  Every generator reads every page; the
+//                      page's owner (page q: generator q mod 9) keeps the events
+//                      whose cylinder reaches the tile, compacting the page in
+//                      place, and records per chunk of 16 kept events the T
+//                      columns their windows cover.  Each chunk becomes one
+//                      "entry" per column window of up to 80 columns of a
+//                      CTA-wide sequence; entry e is built by generator e mod 9
+//                      into stage e mod 12 of a shared ring: A = K_s and B = K_t
+//                      as hi and lo 16-bit tiles in the tensor cores' shared
+//                      memory layout, handed to the MMA warp one stage at a time.
+//   warps 12-15        epilogue: one per tensor-memory lane quarter; scales by
+//                      c_s c_t / (n hs^2 ht), writes each voxel of the tile (vector
+//                      stores), adds later segments, zeroes the accumulator
 // Two accumulators of 256 columns let the epilogue of one segment overlap the
-// MMAs of the next.  The MMA thread consumes pages, and the chunks of a page, in
-// order, so every voxel sums its events in the same order on every run
-// (bit-reproducible, no global atomics).  The generator of the earliest
-// unconsumed chunk can always build it, so no wait can close a cycle.
+// MMAs of the next.  The MMA warp consumes the entries strictly in sequence, so
+// every voxel sums its events in the same order on every run (bit-reproducible,
+// no global atomics).  The builder of the earliest unbuilt entry only waits on
+// earlier entries, so no wait can close a cycle.
 //
 // Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
 // kernel sets the timeout bit of the error word, every role leaves its loop,
@@ -59,81 +63,138 @@ namespace {
 
 constexpr int NB = 256;            // T columns per tile = accumulator width
 constexpr int NACC = 2;            // accumulators (512 tensor-memory columns)
-constexpr int NGEN = 8;            // generator warps
+constexpr int NGEN = 9;            // generator warps
 constexpr int NEPI = 4;            // epilogue warps
 constexpr int WARP_MMA = 0;
 constexpr int WARP_LOAD = 4;
 constexpr int WARP_EPI0 = 12;
 constexpr int NTHREADS = 16 * 32;
 constexpr int PAGE = 256;          // events per staging page
-constexpr int NPAGES = 12;
+constexpr int NPAGES = 6;
 constexpr int CHUNK = 16;          // events per MMA (K of kind::f16)
-constexpr int NCAP = 128;          // T columns per operand stage (one column window)
-constexpr int TAB_ROW = 144;       // bytes per factor-table row (16 float2 + pad: no bank conflicts)
+constexpr int MAXCH = PAGE / CHUNK;
+constexpr int MAXENT = 64;         // entries per page: 16 chunks x at most 4 windows
+constexpr int NCAP = 80;           // T columns per entry (one column window)
+constexpr int BATCH = 1;           // entries per hand-off to the MMA warp (measured best)
+constexpr int NBATCH = 12;
+constexpr int NSTAGE = BATCH * NBATCH;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr uint64_t DRAIN_NS = 200000000ull;
 constexpr uint32_t A_BYTES = TILE_XY * CHUNK * 2;   // 4 KB
-constexpr uint32_t B_BYTES = NCAP * CHUNK * 2;      // 4 KB
+constexpr uint32_t B_BYTES = NCAP * CHUNK * 2;      // 2.5 KB
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr uint32_t TAB_BYTES = 3584;                // x table, y table, t values
 constexpr uint32_t CORE_LBO = 128;  // next core matrix along K
 constexpr uint32_t CORE_SBO = 256;  // next core matrix along M / N
+// per-generator factor tables (rows padded so the A loop's reads hit distinct banks)
+constexpr int XA_STRIDE = 20;       // floats per x row: 1 - u^2 for 16 events
+constexpr int YB_STRIDE = 36;       // floats per y row: 1 - v^2, then v^2, for 16 events
+constexpr uint32_t TAB_XA = 0;
+constexpr uint32_t TAB_YB = TX * XA_STRIDE * 4;
+constexpr uint32_t TAB_TK = TAB_YB + TY * YB_STRIDE * 4;
+constexpr uint32_t TAB_BYTES = TAB_TK + 128;
 
-// page and stage header flags
-constexpr int F_MMA = 1;        // stage holds operands for the MMA
-constexpr int F_PAGE_END = 2;   // last stage of a page
-constexpr int F_ITEM_END = 4;   // last page / stage of a tile
-constexpr int F_TERM = 8;       // page: no more tiles
-constexpr int F_MORE = 16;      // stage: another column window of the same chunk follows
+// entry header flags
+constexpr int F_MMA = 1;        // the stage holds operands for the MMA
+constexpr int F_ITEM_END = 4;   // last entry of a tile
+constexpr int F_TERM = 8;       // end of the CTA's sequence (and padding after it)
+// page meta flags (written by the loader)
+constexpr int P_ITEM_END = 4;
+constexpr int P_TERM = 8;
 
 // generator index of a warp (-1: not a generator)
 __device__ __forceinline__ int gen_index(int warp) {
     return (warp >= 1 && warp <= 3) ? warp - 1 : (warp >= 5 && warp <= 7) ? warp - 2
-         : (warp == 9 || warp == 10) ? warp - 3 : -1;
+         : (warp >= 9 && warp <= 11) ? warp - 3 : -1;
 }
 
 struct L {
     static constexpr uint32_t OFF_STAGE = 0;
-    static constexpr uint32_t OFF_PAGES = OFF_STAGE + NGEN * STAGE_BYTES;
+    static constexpr uint32_t OFF_PAGES = OFF_STAGE + NSTAGE * STAGE_BYTES;
     static constexpr uint32_t OFF_TAB = OFF_PAGES + NPAGES * PAGE * 16;
-    static constexpr uint32_t OFF_SHDR = OFF_TAB + NGEN * TAB_BYTES;
-    static constexpr uint32_t OFF_PMETA = OFF_SHDR + NGEN * 32;
-    static constexpr uint32_t OFF_KEPT = OFF_PMETA + NPAGES * 16;
-    static constexpr uint32_t OFF_DESC = OFF_KEPT + NPAGES * 16;
+    static constexpr uint32_t OFF_HDR = OFF_TAB + NGEN * TAB_BYTES;
+    static constexpr uint32_t OFF_PMETA = OFF_HDR + NSTAGE * 32;
+    static constexpr uint32_t OFF_KEPT = OFF_PMETA + NPAGES * 32;
+    static constexpr uint32_t OFF_CTAB = OFF_KEPT + NPAGES * 16;
+    static constexpr uint32_t OFF_ENT = OFF_CTAB + NPAGES * MAXCH * 8;
+    static constexpr uint32_t OFF_DESC = OFF_ENT + NPAGES * MAXENT * 2;
     static constexpr uint32_t OFF_BAR = OFF_DESC + NACC * 16;
-    static constexpr int NBARS = 3 * NPAGES + 2 * NGEN + 3 * NACC + 1;
+    static constexpr int NBARS = 3 * NPAGES + 2 * NBATCH + 3 * NACC + 1;
     static constexpr uint32_t OFF_MISC = OFF_BAR + NBARS * 8;
     static constexpr uint32_t TOTAL = OFF_MISC + 16;
     __host__ __device__ static constexpr int pfull(int p) { return p; }
     __host__ __device__ static constexpr int pempty(int p) { return NPAGES + p; }
     __host__ __device__ static constexpr int pfilt(int p) { return 2 * NPAGES + p; }
-    __host__ __device__ static constexpr int sfull(int g) { return 3 * NPAGES + g; }
-    __host__ __device__ static constexpr int sempty(int g) { return 3 * NPAGES + NGEN + g; }
-    __host__ __device__ static constexpr int afull(int b) { return 3 * NPAGES + 2 * NGEN + b; }
-    __host__ __device__ static constexpr int aempty(int b) { return 3 * NPAGES + 2 * NGEN + NACC + b; }
-    __host__ __device__ static constexpr int dfull(int b) { return 3 * NPAGES + 2 * NGEN + 2 * NACC + b; }
-    __host__ __device__ static constexpr int drain() { return 3 * NPAGES + 2 * NGEN + 3 * NACC; }
+    __host__ __device__ static constexpr int bfull(int b) { return 3 * NPAGES + b; }
+    __host__ __device__ static constexpr int bempty(int b) { return 3 * NPAGES + NBATCH + b; }
+    __host__ __device__ static constexpr int afull(int a) { return 3 * NPAGES + 2 * NBATCH + a; }
+    __host__ __device__ static constexpr int aempty(int a) { return 3 * NPAGES + 2 * NBATCH + NACC + a; }
+    __host__ __device__ static constexpr int dfull(int a) { return 3 * NPAGES + 2 * NBATCH + 2 * NACC + a; }
+    __host__ __device__ static constexpr int drain() { return 3 * NPAGES + 2 * NBATCH + 3 * NACC; }
     static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
+    static_assert(TAB_BYTES % 16 == 0 && OFF_PAGES % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
     static_assert(TOTAL <= 227 * 1024, "shared memory budget");
-    static_assert(TAB_BYTES >= (TX + TY) * TAB_ROW + CHUNK * 4, "table size");
+    static_assert(NCAP % 16 == 0 && NCAP <= NB, "column window");
+    // a generator's consecutive entries are NGEN apart; for its stage waits to
+    // be at most one barrier phase behind, NGEN entries may span at most NBATCH
+    // batches
+    static_assert(NGEN <= BATCH * (NBATCH - 1) + 1, "stage ring too short for the generators");
 };
 
-// hi + lo split of two values into packed 16-bit pairs (low half = first value).
+__device__ __forceinline__ float2 fneg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <typename T>
+__device__ __forceinline__ uint32_t bits32(const T& v) {
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Two sign masks as one word: low 16 bits all ones if a < 0 (or -0), high 16
+// bits all ones if b < 0 (prmt's sign-replicating byte select).
+__device__ __forceinline__ uint32_t sign_mask2(float a, float b) {
+    uint32_t m;
+    asm("prmt.b32 %0, %1, %2, 0xFFBB;" : "=r"(m) : "r"(__float_as_uint(a)), "r"(__float_as_uint(b)));
+    return m;
+}
+
+// hi = round-to-nearest 16-bit value of v, lo = rounded remainder, both packed
+// (low half = v.x).
 template <bool FP16>
-__device__ __forceinline__ void split2(float a0, float a1, uint32_t& hi, uint32_t& lo) {
+__device__ __forceinline__ void split_rn(float2 v, uint32_t& hi, uint32_t& lo) {
     if constexpr (FP16) {
-        const __half2 h = __floats2half2_rn(a0, a1);
-        const float2 hf = __half22float2(h);
-        const __half2 l = __floats2half2_rn(a0 - hf.x, a1 - hf.y);
-        hi = *reinterpret_cast<const uint32_t*>(&h);
-        lo = *reinterpret_cast<const uint32_t*>(&l);
+        const __half2 h = __floats2half2_rn(v.x, v.y);
+        const float2 r = __fadd2_rn(v, fneg2(__half22float2(h)));
+        hi = bits32(h);
+        lo = bits32(__floats2half2_rn(r.x, r.y));
     } else {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(a0 - hf.x, a1 - hf.y);
-        hi = *reinterpret_cast<const uint32_t*>(&h);
-        lo = *reinterpret_cast<const uint32_t*>(&l);
+        const uint32_t h = bits32(__floats2bfloat162_rn(v.x, v.y));
+        const float2 hf = make_float2(__uint_as_float(h << 16), __uint_as_float(h & 0xffff0000u));
+        const float2 r = __fadd2_rn(v, fneg2(hf));
+        hi = h;
+        lo = bits32(__floats2bfloat162_rn(r.x, r.y));
     }
+}
+
+// The three products of one entry, issued by one elected lane of a converged warp:
+// D += Ahi*Bhi, D += Ahi*Blo, D += Alo*Bhi.
+__device__ __forceinline__ void mma3_elect(uint32_t d, uint64_t ahi, uint64_t alo, uint64_t bhi,
+                                           uint64_t blo, uint32_t idesc) {
+    asm volatile(
+        "{\n\t.reg .pred e, acc;\n\t"
+        "setp.ne.b32 acc, 1, 0;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %3, %5, acc;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %4, %5, acc;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %5, acc;\n\t}"
+        ::"r"(d), "l"(ahi), "l"(alo), "l"(bhi), "l"(blo), "r"(idesc)
+        : "memory");
+}
+
+// tcgen05.commit by one elected lane of a converged warp.
+__device__ __forceinline__ void commit_elect(uint32_t bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}"
+        ::"r"(bar) : "memory");
 }
 
 struct Ctl {
@@ -190,6 +251,10 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Ctl c{reinterpret_cast<volatile int*>(smem + L::OFF_MISC + 4), err};
     auto bar = [sb](int i) -> uint32_t { return sb + L::OFF_BAR + 8u * (uint32_t)i; };
+    int4* pmeta = reinterpret_cast<int4*>(smem + L::OFF_PMETA);
+    int4* pkept = reinterpret_cast<int4*>(smem + L::OFF_KEPT);
+    int2* ctab = reinterpret_cast<int2*>(smem + L::OFF_CTAB);
+    uint16_t* pent = reinterpret_cast<uint16_t*>(smem + L::OFF_ENT);
 
     if (threadIdx.x == 0) {
         for (int p = 0; p < NPAGES; ++p) {
@@ -197,14 +262,14 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             ptx::mbar_init(bar(L::pempty(p)), NGEN);
             ptx::mbar_init(bar(L::pfilt(p)), 1);
         }
-        for (int g = 0; g < NGEN; ++g) {
-            ptx::mbar_init(bar(L::sfull(g)), 1);
-            ptx::mbar_init(bar(L::sempty(g)), 1);
+        for (int b = 0; b < NBATCH; ++b) {
+            ptx::mbar_init(bar(L::bfull(b)), BATCH);
+            ptx::mbar_init(bar(L::bempty(b)), 1);
         }
-        for (int b = 0; b < NACC; ++b) {
-            ptx::mbar_init(bar(L::afull(b)), 1);
-            ptx::mbar_init(bar(L::aempty(b)), NEPI);
-            ptx::mbar_init(bar(L::dfull(b)), 1);
+        for (int a = 0; a < NACC; ++a) {
+            ptx::mbar_init(bar(L::afull(a)), 1);
+            ptx::mbar_init(bar(L::aempty(a)), NEPI);
+            ptx::mbar_init(bar(L::dfull(a)), 1);
         }
         ptx::mbar_init(bar(L::drain()), 1);
         *c.abort = 0;
@@ -230,12 +295,13 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             fill = 0;
             return true;
         };
-        auto close_page = [&](int flags, int64_t item) {
+        // page meta: fill, flags, item, and the item's tile coordinates
+        auto close_page = [&](int flags, int64_t item, int tx, int ty, int tb) {
             __syncwarp();
             if (lane == 0) {
                 const uint32_t p = pg % NPAGES;
-                ptx::sts_i4(sb + L::OFF_PMETA + p * 16,
-                            make_int4((int)fill, flags, (int)(item & 0xffffffff), (int)(item >> 32)));
+                pmeta[2 * p] = make_int4((int)fill, flags, (int)(item & 0xffffffff), (int)(item >> 32));
+                pmeta[2 * p + 1] = make_int4(tx, ty, tb, 0);
                 ptx::mbar_arrive(bar(L::pfull(p)));
             }
             __syncwarp();
@@ -281,41 +347,44 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                     }
                     fill += take;
                     done += take;
-                    if (fill == (uint32_t)PAGE) close_page(0, item);
+                    if (fill == (uint32_t)PAGE) close_page(0, item, tx, ty, tb);
                 }
             }
             if (!ok) break;
             if (!open && !(ok = open_page())) break;
-            close_page(F_ITEM_END, item);  // the tile's last page, possibly empty
+            close_page(P_ITEM_END, item, tx, ty, tb);  // the tile's last page, possibly empty
         }
         // termination page (every generator reads every page)
-        if (ok && (ok = open_page())) close_page(F_TERM, 0);
+        if (ok && (ok = open_page())) close_page(P_TERM, 0, 0, 0, 0);
         if (!ok) {
-            if (open) close_page(F_TERM, 0);
+            if (open) close_page(P_TERM, 0, 0, 0, 0);
             for (uint32_t q = (pg > NPAGES ? pg - NPAGES : 0); q < pg; ++q)
                 drain_bar(bar(L::pfull(q % NPAGES)), (q / NPAGES) & 1u);
         }
     } else if (gi >= 0) {
         // -------------------------------------------------------- generators
-        // Every generator reads every page.  The page's owner (page q: generator
-        // q mod 8) keeps the events whose cylinder reaches the tile, compacting
-        // them in place; chunk c of page q (events 16c .. 16c+15 of the kept list)
-        // is then built by generator (q + c) mod 8 into its own stage.
-        const uint32_t tab = sb + L::OFF_TAB + gi * TAB_BYTES;
-        const uint32_t tabx = tab, taby = tab + TX * TAB_ROW, tt = tab + (TX + TY) * TAB_ROW;
-        const uint32_t stg = sb + L::OFF_STAGE + gi * STAGE_BYTES;
-        const uint32_t a_hi = stg, a_lo = stg + A_BYTES, b_hi = stg + 2 * A_BYTES,
-                       b_lo = b_hi + B_BYTES;
-        const uint32_t shdr = sb + L::OFF_SHDR + gi * 32;
+        uint8_t* tab = smem + L::OFF_TAB + gi * TAB_BYTES;
+        float* xa = reinterpret_cast<float*>(tab + TAB_XA);
+        float* yb = reinterpret_cast<float*>(tab + TAB_YB);
+        float* tkt = reinterpret_cast<float*>(tab + TAB_TK);
         const uint32_t lt = (1u << lane) - 1u;
-        const float csct = pl.cs * pl.ct;
-        uint32_t suse = 0;  // uses of this warp's stage
+        const float inv_hs = pl.inv_hs, inv_ht = pl.inv_ht;
+        const uint32_t fmt = FP16 ? 0u : 1u;
         bool ok = true;
-        // hands the stage to the MMA thread, with what it needs precomputed: the
+        uint32_t ebase = 0;  // sequence entries before the current page
+        uint32_t emod = 0;   // ebase mod NGEN
+
+        // waits until entry e's stage is free (its previous batch consumed)
+        auto slot_wait = [&](uint32_t e) -> bool {
+            const uint32_t bt = e / BATCH, use = bt / NBATCH;
+            if (use == 0) return true;
+            return wait_warp(c, bar(L::bempty(bt % NBATCH)), (use - 1u) & 1u);
+        };
+        // hands entry e to the MMA warp, with what it needs precomputed: the
         // instruction descriptor, the 32-column blocks the MMAs touch and the
         // per-block chunk-count increments (bytes, four blocks per word)
-        const uint32_t fmt = FP16 ? 0u : 1u;
-        auto publish = [&](int c0, int ncols, int flags) {
+        auto publish = [&](uint32_t e, int c0, int ncols, int flags, int64_t item) {
+            const uint32_t s = e % NSTAGE;
             if (lane == 0) {
                 uint32_t idesc = 0, mask = 0, inc_lo = 0, inc_hi = 0;
                 if (flags & F_MMA) {
@@ -325,44 +394,95 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                     inc_lo = ((mask & 15u) * 0x204081u) & 0x01010101u;
                     inc_hi = ((mask >> 4) * 0x204081u) & 0x01010101u;
                 }
-                ptx::sts_i4(shdr, make_int4(c0, ncols, flags, 0));
-                ptx::sts_i4(shdr + 16, make_int4((int)idesc, (int)mask, (int)inc_lo, (int)inc_hi));
+                int4* h = reinterpret_cast<int4*>(smem + L::OFF_HDR + s * 32);
+                h[0] = make_int4(c0, (int)idesc, flags, (int)mask);
+                h[1] = make_int4((int)inc_lo, (int)inc_hi, (int)(item & 0xffffffff), (int)(item >> 32));
             }
             ptx::fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(bar(L::sfull(gi)));
-            ++suse;
+            if (lane == 0) ptx::mbar_arrive(bar(L::bfull((e / BATCH) % NBATCH)));
         };
         // Keeps the events of page fq (staged, owned by this generator) whose
-        // cylinder reaches their tile, compacted in place, and publishes the count.
+        // cylinder reaches their tile, compacted in place; records per chunk the
+        // covered columns and the chunk's first sequence entry; publishes the
+        // kept and entry counts.
         uint32_t filt_next = (uint32_t)gi;  // next owned page not yet filtered
         auto filter_page = [&](uint32_t fq) {
             const uint32_t fp = fq % NPAGES;
-            const uint32_t fb = sb + L::OFF_PAGES + fp * PAGE * 16;
-            const int4 fm = ptx::lds_i4(sb + L::OFF_PMETA + fp * 16);
-            uint32_t kept = 0;
-            if (!(fm.y & F_TERM)) {
-                const int64_t fitem = (int64_t)(uint32_t)fm.z | ((int64_t)fm.w << 32);
-                int ftx, fty, ftb;
-                decode_item(pl, fitem, ftx, fty, ftb);
-                const TileGeom fg = tile_geom(pl, ftx, fty, ftb, NB);
+            float4* fb = reinterpret_cast<float4*>(smem + L::OFF_PAGES + fp * PAGE * 16);
+            int2* ct = ctab + fp * MAXCH;
+            uint16_t* ent = pent + fp * MAXENT;
+            const int4 fm = pmeta[2 * fp], fmt4 = pmeta[2 * fp + 1];
+            uint32_t kept = 0, nent = 0;
+            if (!(fm.y & P_TERM)) {
+                const TileGeom fg = tile_geom(pl, fmt4.x, fmt4.y, fmt4.z, NB);
                 for (int r = 0; r * 32 < fm.x; ++r) {
                     const int slot = r * 32 + lane;
                     float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
                     bool keep = false;
                     if (slot < fm.x) {
-                        e = ptx::lds_f4(fb + slot * 16u);
+                        e = fb[slot];
                         keep = reaches(pl, fg, e);
                     }
                     const uint32_t bal = __ballot_sync(0xffffffffu, keep);
                     __syncwarp();
-                    if (keep) ptx::sts_f4(fb + (kept + __popc(bal & lt)) * 16u, e);
+                    if (keep) fb[kept + __popc(bal & lt)] = e;
                     kept += __popc(bal);
                     __syncwarp();
                 }
+                // columns covered by each chunk's windows, clipped into the block
+                // (the filter's margin can keep an event whose window misses the
+                // block; its K_t values are zero anyway)
+                const int nch = (int)(kept + CHUNK - 1) / CHUNK;
+                const int T0 = fg.T0, nbv = fg.T1 - fg.T0;
+                for (int r = 0; r * 32 < (int)kept; ++r) {
+                    const int slot = r * 32 + lane;
+                    int lo = 0x7fffffff, hi = -1;
+                    if (slot < (int)kept) {
+                        const float z = fb[slot].z;
+                        lo = min(max((int)ceilf(z - 0.5f - pl.htv) - T0, 0), nbv - 1);
+                        hi = min(max((int)floorf(z - 0.5f + pl.htv) - T0, lo), nbv - 1);
+                    }
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) {
+                        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                    }
+                    const int ch = 2 * r + (lane >> 4);
+                    if ((lane & 15) == 0 && ch < nch)
+                        ct[ch] = make_int2((lo & ~15) | (((hi + 16) & ~15) << 16), 0);
+                }
+                __syncwarp();
+                // entries per chunk (column windows of up to NCAP) and their offsets
+                uint32_t nw = 0;
+                if (lane < nch) {
+                    const int2 t = ct[lane];
+                    nw = (uint32_t)(((t.x >> 16) - (t.x & 0xffff) + NCAP - 1) / NCAP);
+                }
+                uint32_t incl = nw;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                // entry table: entry j of the page -> (chunk, window)
+                if (lane < nch) {
+                    ct[lane].y = (int)((incl - nw) | (nw << 16));
+                    for (uint32_t w = 0; w < nw; ++w) ent[incl - nw + w] = (uint16_t)(lane | (w << 8));
+                }
+                nent = __shfl_sync(0xffffffffu, incl, 31);
+                // a tile whose last page adds nothing still needs its end marker
+                if (nent == 0 && (fm.y & P_ITEM_END)) {
+                    nent = 1;
+                    if (lane == 0) ent[0] = 0xffffu;
+                }
             }
+            // the compaction wrote the page: order it before the loader's next
+            // bulk copy into the page
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
             if (lane == 0) {
-                ptx::sts_i4(sb + L::OFF_KEPT + fp * 16, make_int4((int)kept, 0, 0, 0));
+                pkept[fp] = make_int4((int)kept, (int)nent, 0, 0);
                 ptx::mbar_arrive(bar(L::pfilt(fp)));
             }
             __syncwarp();
@@ -380,220 +500,249 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
         for (uint32_t q = 0; ok; ++q) {
             const uint32_t p = q % NPAGES;
             const uint32_t ph = (q / NPAGES) & 1u;
-            const uint32_t pgb = sb + L::OFF_PAGES + p * PAGE * 16;
+            const float4* page = reinterpret_cast<const float4*>(smem + L::OFF_PAGES + p * PAGE * 16);
             if (!(ok = wait_warp(c, bar(L::pfull(p)), ph))) break;
-            const int4 meta = ptx::lds_i4(sb + L::OFF_PMETA + p * 16);
-            if (meta.y & F_TERM) break;
+            const int4 meta = pmeta[2 * p], mt = pmeta[2 * p + 1];
+            if (meta.y & P_TERM) {
+                // the sequence ends with entry ebase; entries to the end of its batch are padding
+                const uint32_t eend = (ebase / BATCH + 1u) * BATCH;
+                for (uint32_t e = ebase; e < eend && ok; ++e) {
+                    if (e % NGEN != (uint32_t)gi) continue;
+                    if (!(ok = slot_wait(e))) break;
+                    publish(e, 0, 0, F_TERM, 0);
+                }
+                break;
+            }
             const int64_t item = (int64_t)(uint32_t)meta.z | ((int64_t)meta.w << 32);
-            const int end = meta.y & F_ITEM_END;
-            int tx, ty, tb;
-            decode_item(pl, item, tx, ty, tb);
-            const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
-            const int X0 = g.X0, Y0 = g.Y0, T0 = g.T0, nbv = g.T1 - g.T0;
+            const int end = meta.y & P_ITEM_END;
+            const int X0 = mt.x * TX, Y0 = mt.y * TY, T0 = mt.z * NB;
             if ((int)(q % NGEN) == gi && q >= filt_next) {
                 // this generator owns page q and has not filtered it ahead: do it now
                 filter_page(q);
             } else if (!(ok = wait_warp(c, bar(L::pfilt(p)), ph))) {
                 break;
             }
-            const int kept = ptx::lds_i4(sb + L::OFF_KEPT + p * 16).x;
+            const int4 ki = pkept[p];
+            const int kept = ki.x;
+            const uint32_t nent = (uint32_t)ki.y;
             const int nch = (kept + CHUNK - 1) / CHUNK;
-            if (nch == 0 && (int)(q % NGEN) == gi) {  // nothing to add: just mark the page's end
-                if (!(ok = wait_warp(c, bar(L::sempty(gi)), (suse & 1u) ^ 1u))) break;
-                publish(0, 0, F_PAGE_END | end);
-            }
-            for (int ch = (int)((gi - (int)(q % NGEN) + NGEN) % NGEN); ch < nch && ok; ch += NGEN) {
+            const int2* ct = ctab + p * MAXCH;
+            const uint16_t* ent = pent + p * MAXENT;
+            // entry e is always built by generator e mod NGEN, so each generator's
+            // entries are exactly NGEN apart and its stage waits are never more
+            // than one barrier phase behind
+            for (uint32_t j = ((uint32_t)gi + NGEN - emod) % NGEN; j < nent && ok; j += NGEN) {
+                const uint32_t e = ebase + j;
+                const uint32_t code = ent[j];
+                if (code == 0xffffu) {
+                    // end marker of a tile whose last page keeps nothing
+                    if (!(ok = slot_wait(e))) break;
+                    publish(e, 0, 0, F_ITEM_END, item);
+                    continue;
+                }
+                const int ch = (int)(code & 0xffu), w = (int)(code >> 8);
+                const int2 cinfo = ct[ch];
+                const int nw = cinfo.y >> 16;
+                const int c0 = cinfo.x & 0xffff, cend = cinfo.x >> 16;
                 filter_ahead(q);
                 const int count = min(CHUNK, kept - ch * CHUNK);
-                float4 e = make_float4(1.0e30f, 1.0e30f, 1.0e30f, 0.f);
-                if (lane < count) e = ptx::lds_f4(pgb + (ch * CHUNK + lane) * 16u);
-                // columns the events' T windows cover, clipped into the block (the
-                // filter's margin can keep an event whose window misses the block;
-                // its K_t values are zero anyway)
-                int lo = 0x7fffffff, hi = -1;
-                if (lane < count) {
-                    lo = min(max((int)ceilf(e.z - 0.5f - pl.htv) - T0, 0), nbv - 1);
-                    hi = min(max((int)floorf(e.z - 0.5f + pl.htv) - T0, lo), nbv - 1);
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-                }
-                const int c0 = lo & ~15;
-                const int cend = ((hi + 1) + 15) & ~15;  // exclusive, <= roundup16(nbv) <= NB
 
-                // factor tables of K_s: (u^2, 1-u^2) per x and (v^2, 1-v^2) per y
+                // factor tables of K_s for the chunk's 16 events (missing events
+                // get u, v >= 2: negative factors, masked below)
+                const int k = lane & 15, half = lane >> 4;
+                const bool real = k < count;
+                float4 ek = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (real) ek = page[ch * CHUNK + k];
+                const float cu = real ? ((float)X0 + 0.5f - ek.x) * inv_hs : 2.0f;
+                const float cv = real ? ((float)Y0 + 0.5f - ek.y) * inv_hs : 2.0f;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int qq = i * 32 + lane, x = qq >> 4, k = qq & 15;
-                    const float ex = __shfl_sync(0xffffffffu, e.x, k);
-                    const float du = ((float)(X0 + x) + 0.5f - ex) * pl.inv_hs;
-                    const float u2 = du * du;
-                    ptx::sts_f2(tabx + x * TAB_ROW + k * 8, make_float2(u2, 1.0f - u2));
+                for (int i = 0; i < TX / 2; ++i) {
+                    const int x = half + 2 * i;
+                    const float u = fmaf((float)x, inv_hs, cu);
+                    xa[x * XA_STRIDE + k] = fmaf(-u, u, 1.0f);
                 }
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int qq = i * 32 + lane, y = qq >> 4, k = qq & 15;
-                    const float ey = __shfl_sync(0xffffffffu, e.y, k);
-                    const float dv = ((float)(Y0 + y) + 0.5f - ey) * pl.inv_hs;
-                    const float v2 = dv * dv;
-                    ptx::sts_f2(taby + y * TAB_ROW + k * 8, make_float2(v2, 1.0f - v2));
+                for (int i = 0; i < TY / 2; ++i) {
+                    const int y = half + 2 * i;
+                    const float v = fmaf((float)y, inv_hs, cv);
+                    const float vv = v * v;
+                    yb[y * YB_STRIDE + k] = 1.0f - vv;
+                    yb[y * YB_STRIDE + 16 + k] = vv;
                 }
-                if (lane < CHUNK) ptx::sts_f(tt + lane * 4, e.z);
-                __syncwarp();
-
-                if (!(ok = wait_warp(c, bar(L::sempty(gi)), (suse & 1u) ^ 1u))) break;
-                // A = K_s without c_s: row r = voxel (x = r / 8, y = r % 8); lane owns
-                // rows lane + 32 j, all with y = lane % 8
-#pragma unroll
-                for (int kg = 0; kg < 2; ++kg) {
-                    float4 fy[4];
-#pragma unroll
-                    for (int kp = 0; kp < 4; ++kp)
-                        fy[kp] = ptx::lds_f4(taby + (lane & 7) * TAB_ROW + (kg * 8 + 2 * kp) * 8);
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        const int r = lane + 32 * jj;
-                        uint32_t ah[4], al[4];
-#pragma unroll
-                        for (int kp = 0; kp < 4; ++kp) {
-                            const float4 fx = ptx::lds_f4(tabx + (r >> 3) * TAB_ROW + (kg * 8 + 2 * kp) * 8);
-                            const float a0 = (fx.x + fy[kp].x < 1.0f) ? fx.y * fy[kp].y : 0.0f;
-                            const float a1 = (fx.z + fy[kp].z < 1.0f) ? fx.w * fy[kp].w : 0.0f;
-                            split2<FP16>(a0, a1, ah[kp], al[kp]);
-                        }
-                        const uint32_t off = (uint32_t)(r >> 3) * CORE_SBO + kg * CORE_LBO + (r & 7) * 16;
-                        ptx::sts_u4(a_hi + off, ah[0], ah[1], ah[2], ah[3]);
-                        ptx::sts_u4(a_lo + off, al[0], al[1], al[2], al[3]);
-                    }
-                }
-                // B = c_s c_t (1 - w^2)_+ in column windows of up to NCAP
-                float tk[CHUNK];
-#pragma unroll
-                for (int k4 = 0; k4 < CHUNK / 4; ++k4) {
-                    const float4 t4 = ptx::lds_f4(tt + k4 * 16);
-                    tk[4 * k4] = t4.x; tk[4 * k4 + 1] = t4.y; tk[4 * k4 + 2] = t4.z; tk[4 * k4 + 3] = t4.w;
-                }
-                for (int cw = c0; cw < cend && ok; cw += NCAP) {
-                    if (cw != c0 && !(ok = wait_warp(c, bar(L::sempty(gi)), (suse & 1u) ^ 1u))) break;
+                {
+                    const int cw = c0 + w * NCAP;
                     const int ncols = min(NCAP, cend - cw);
-                    for (int n = lane; n < ncols; n += 32) {
-                        const float tc = (float)(T0 + cw + n) + 0.5f;
+                    // event time relative to the window's first voxel centre
+                    if (lane < CHUNK)
+                        tkt[lane] = real ? ek.z - ((float)(T0 + cw) + 0.5f) : 1.0e9f;
+                    __syncwarp();
+                    if (!(ok = slot_wait(e))) break;
+                    uint8_t* st = smem + L::OFF_STAGE + (e % NSTAGE) * STAGE_BYTES;
+
+                    // A = K_s without c_s: row r = voxel (x = r / 8, y = r % 8); lane
+                    // owns rows lane + 32 j, all with y = lane % 8.  The disk test
+                    // (u^2 + v^2 < 1, i.e. (1 - u^2) - v^2 > 0) masks both halves.
+                    {
+                        const float* yrow = yb + (lane & 7) * YB_STRIDE;
+                        float2 bq[8], vq[8];
 #pragma unroll
-                        for (int kg = 0; kg < 2; ++kg) {
-                            uint32_t bh[4], bl[4];
+                        for (int i = 0; i < 4; ++i) {
+                            const float4 tb4 = *reinterpret_cast<const float4*>(yrow + 4 * i);
+                            const float4 tv4 = *reinterpret_cast<const float4*>(yrow + 16 + 4 * i);
+                            bq[2 * i] = make_float2(tb4.x, tb4.y);
+                            bq[2 * i + 1] = make_float2(tb4.z, tb4.w);
+                            vq[2 * i] = make_float2(tv4.x, tv4.y);
+                            vq[2 * i + 1] = make_float2(tv4.z, tv4.w);
+                        }
 #pragma unroll
-                            for (int kp = 0; kp < 4; ++kp) {
-                                const float w0 = (tc - tk[kg * 8 + 2 * kp]) * pl.inv_ht;
-                                const float w1 = (tc - tk[kg * 8 + 2 * kp + 1]) * pl.inv_ht;
-                                const float b0 = csct * fmaxf(fmaf(-w0, w0, 1.0f), 0.0f);
-                                const float b1 = csct * fmaxf(fmaf(-w1, w1, 1.0f), 0.0f);
-                                split2<FP16>(b0, b1, bh[kp], bl[kp]);
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const float* xrow = xa + ((lane >> 3) + 4 * jj) * XA_STRIDE;
+                            uint32_t ah[8], al[8];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const float4 t4 = *reinterpret_cast<const float4*>(xrow + 4 * i);
+                                const float2 aq[2] = {make_float2(t4.x, t4.y), make_float2(t4.z, t4.w)};
+#pragma unroll
+                                for (int h = 0; h < 2; ++h) {
+                                    const int pp = 2 * i + h;
+                                    const float2 pr = __fmul2_rn(aq[h], bq[pp]);
+                                    const float2 d = __fadd2_rn(aq[h], fneg2(vq[pp]));
+                                    split_rn<FP16>(pr, ah[pp], al[pp]);
+                                    const uint32_t m = sign_mask2(d.x, d.y);
+                                    ah[pp] &= ~m;
+                                    al[pp] &= ~m;
+                                }
                             }
-                            const uint32_t off = (uint32_t)(n >> 3) * CORE_SBO + kg * CORE_LBO + (n & 7) * 16;
-                            ptx::sts_u4(b_hi + off, bh[0], bh[1], bh[2], bh[3]);
-                            ptx::sts_u4(b_lo + off, bl[0], bl[1], bl[2], bl[3]);
+                            const int r = lane + 32 * jj;
+                            const uint32_t off = (uint32_t)(r >> 3) * CORE_SBO + (uint32_t)(r & 7) * 16;
+                            *reinterpret_cast<uint4*>(st + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
+                            *reinterpret_cast<uint4*>(st + off + CORE_LBO) = make_uint4(ah[4], ah[5], ah[6], ah[7]);
+                            *reinterpret_cast<uint4*>(st + A_BYTES + off) = make_uint4(al[0], al[1], al[2], al[3]);
+                            *reinterpret_cast<uint4*>(st + A_BYTES + off + CORE_LBO) =
+                                make_uint4(al[4], al[5], al[6], al[7]);
                         }
                     }
-                    const bool more = cw + NCAP < cend;
-                    const int fl = F_MMA | (more ? F_MORE : 0) |
-                                   ((!more && ch == nch - 1) ? (F_PAGE_END | end) : 0);
-                    publish(cw, ncols, fl);
+                    // B = K_t without c_t: (1 - w^2)_+ for the window's columns
+                    {
+                        float2 tq[8];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float4 t4 = *reinterpret_cast<const float4*>(tkt + 4 * i);
+                            tq[2 * i] = make_float2(-t4.x, -t4.y);
+                            tq[2 * i + 1] = make_float2(-t4.z, -t4.w);
+                        }
+                        const float2 ih2 = make_float2(inv_ht, inv_ht), one2 = make_float2(1.0f, 1.0f);
+                        uint8_t* bh = st + 2 * A_BYTES;
+                        uint8_t* bl = bh + B_BYTES;
+                        for (int n = lane; n < ncols; n += 32) {
+                            const float2 n2 = make_float2((float)n, (float)n);
+                            uint32_t h[8], l[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const float2 wv = __fmul2_rn(__fadd2_rn(n2, tq[i]), ih2);
+                                const float2 kt = __ffma2_rn(fneg2(wv), wv, one2);
+                                split_rn<FP16>(make_float2(fmaxf(kt.x, 0.0f), fmaxf(kt.y, 0.0f)), h[i], l[i]);
+                            }
+                            const uint32_t off = (uint32_t)(n >> 3) * CORE_SBO + (uint32_t)(n & 7) * 16;
+                            *reinterpret_cast<uint4*>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                            *reinterpret_cast<uint4*>(bh + off + CORE_LBO) = make_uint4(h[4], h[5], h[6], h[7]);
+                            *reinterpret_cast<uint4*>(bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                            *reinterpret_cast<uint4*>(bl + off + CORE_LBO) = make_uint4(l[4], l[5], l[6], l[7]);
+                        }
+                    }
+                    const int fl = F_MMA | ((end && ch == nch - 1 && w + 1 == nw) ? F_ITEM_END : 0);
+                    publish(e, cw, ncols, fl, item);
                 }
             }
             if (!ok) break;
-            // done with the page: order these generic accesses before the loader's
-            // next bulk copy into it, then release it
-            ptx::fence_proxy_async_smem();
+            // done with the page (only read here; the owner fenced its compaction)
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(bar(L::pempty(p)));
+            ebase += nent;
+            emod = (emod + nent) % NGEN;
         }
     } else if (warp == WARP_MMA) {
         // --------------------------------------------------------------- MMA
-        if (lane == 0) {
-            uint32_t par = 0;  // bit g: parity of the next use of generator g's stage
-            uint32_t seg = 0;  // accumulator segments opened so far
-            uint32_t qm = 0;   // next page
-            bool ok = true;
-            // descriptors of stage 0; stage g adds g * STAGE_BYTES / 16 to the address field
-            const uint64_t d_ahi = ptx::smem_desc(sb + L::OFF_STAGE, CORE_LBO, CORE_SBO);
-            const uint64_t d_alo = d_ahi + (A_BYTES >> 4);
-            const uint64_t d_bhi = d_ahi + ((2 * A_BYTES) >> 4);
-            const uint64_t d_blo = d_ahi + ((2 * A_BYTES + B_BYTES) >> 4);
-            // chunks per 32-column block before a segment is closed, four blocks per word
-            const uint32_t thr4 = (uint32_t)flush_chunks * 0x01010101u;
-            for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-                int b = (int)(seg & 1u);
-                if (!(ok = wait_bar(c, bar(L::aempty(b)), (seg >> 1) & 1u))) break;
-                ptx::tc_fence_after();
-                int first = 1;
-                uint32_t touched = 0;             // 32-column blocks written in this segment
-                uint32_t cnt_lo = 0, cnt_hi = 0;  // chunks per 32-column block (bytes)
-                int flags = 0;
-                while (!(flags & F_ITEM_END) && ok) {
-                    flags = 0;
-                    for (uint32_t ch = 0; !(flags & F_PAGE_END) && ok; ++ch) {
-                        const int gq = (int)((qm + ch) % NGEN);
-                        flags = F_MORE;
-                        while ((flags & F_MORE) && ok) {
-                            if (!(ok = wait_bar(c, bar(L::sfull(gq)), (par >> gq) & 1u))) break;
-                            par ^= 1u << gq;
-                            const int4 h = ptx::lds_i4(sb + L::OFF_SHDR + gq * 32);
-                            const int4 h1 = ptx::lds_i4(sb + L::OFF_SHDR + gq * 32 + 16);
-                            flags = h.z;
-                            // never issue an MMA outside the accumulator
-                            const bool in_range = (uint32_t)h.x + (uint32_t)h.y <= (uint32_t)NB &&
-                                                  (uint32_t)(h.y - 16) <= (uint32_t)(NCAP - 16) &&
-                                                  ((h.x | h.y) & 15) == 0;
-                            if (!(flags & F_MMA) || !in_range) {
-                                if ((flags & F_MMA) && !in_range) atomicOr(err, ERRBIT_BOUNDS);
-                                ptx::mbar_arrive(bar(L::sempty(gq)));
-                                continue;
-                            }
-                            const uint32_t mask = (uint32_t)h1.y;
-                            const uint32_t inc_lo = (uint32_t)h1.z, inc_hi = (uint32_t)h1.w;
-                            uint32_t n_lo = cnt_lo + inc_lo, n_hi = cnt_hi + inc_hi;
-                            if (__vcmpgtu4(n_lo, thr4) | __vcmpgtu4(n_hi, thr4)) {
-                                // close the segment: the epilogue adds it in fp32
-                                ptx::sts_i4(sb + L::OFF_DESC + b * 16,
-                                            make_int4((int)(item & 0xffffffff), (int)(item >> 32), first, (int)touched));
-                                ptx::mbar_arrive(bar(L::dfull(b)));
-                                ptx::tc_commit(bar(L::afull(b)));
-                                ++seg;
-                                b = (int)(seg & 1u);
-                                if (!(ok = wait_bar(c, bar(L::aempty(b)), (seg >> 1) & 1u))) break;
-                                ptx::tc_fence_after();
-                                first = 0;
-                                touched = 0;
-                                n_lo = inc_lo;
-                                n_hi = inc_hi;
-                            }
-                            cnt_lo = n_lo;
-                            cnt_hi = n_hi;
-                            touched |= mask;
-                            const uint64_t so = (uint64_t)gq * (STAGE_BYTES >> 4);
-                            const uint32_t idesc = (uint32_t)h1.x;
-                            const uint32_t d = tmem + (uint32_t)(b * NB + h.x);
-                            ptx::mma_f16_ss(d, d_ahi + so, d_bhi + so, idesc, 1);
-                            ptx::mma_f16_ss(d, d_ahi + so, d_blo + so, idesc, 1);
-                            ptx::mma_f16_ss(d, d_alo + so, d_bhi + so, idesc, 1);
-                            ptx::tc_commit(bar(L::sempty(gq)));
-                        }
-                    }
-                    ++qm;
-                }
-                if (!ok) break;
+        // The whole warp runs the loop (converged); one elected lane issues.
+        uint32_t nseg = 0;  // accumulator segments closed so far
+        bool ok = true;
+        // descriptors of stage 0; stage s adds s * STAGE_BYTES / 16 to the address field
+        const uint64_t d_ahi = ptx::smem_desc(sb + L::OFF_STAGE, CORE_LBO, CORE_SBO);
+        const uint64_t d_alo = d_ahi + (A_BYTES >> 4);
+        const uint64_t d_bhi = d_ahi + ((2 * A_BYTES) >> 4);
+        const uint64_t d_blo = d_ahi + ((2 * A_BYTES + B_BYTES) >> 4);
+        // chunks per 32-column block at which a segment is closed (a power of
+        // two below 128), as a bit mask over the four byte counters of a word
+        const uint32_t flush4 = (uint32_t)flush_chunks * 0x01010101u;
+        const int4* hdr = reinterpret_cast<const int4*>(smem + L::OFF_HDR);
+        int b = 0;
+        int first = 1;
+        uint32_t touched = 0;             // 32-column blocks written in this segment
+        uint32_t cnt_lo = 0, cnt_hi = 0;  // chunks per 32-column block (bytes)
+        // hands the current segment to the epilogue and opens the next one
+        auto close_segment = [&](int64_t item, int last) -> bool {
+            if (lane == 0) {
                 ptx::sts_i4(sb + L::OFF_DESC + b * 16,
-                            make_int4((int)(item & 0xffffffff), (int)(item >> 32), first | 2, (int)touched));
+                            make_int4((int)(item & 0xffffffff), (int)(item >> 32), first | (last ? 2 : 0),
+                                      (int)touched));
                 ptx::mbar_arrive(bar(L::dfull(b)));
-                ptx::tc_commit(bar(L::afull(b)));
-                ++seg;
             }
-            // every MMA issued has completed before the accumulator is released
-            ptx::tc_commit(bar(L::drain()));
-            drain_bar(bar(L::drain()), 0);
+            __syncwarp();
+            commit_elect(bar(L::afull(b)));
+            ++nseg;
+            b = (int)(nseg & 1u);
+            if (!wait_warp(c, bar(L::aempty(b)), (nseg >> 1) & 1u)) return false;
+            ptx::tc_fence_after();
+            touched = 0;
+            cnt_lo = 0;
+            cnt_hi = 0;
+            return true;
+        };
+        ok = wait_warp(c, bar(L::aempty(0)), 0);
+        ptx::tc_fence_after();
+        for (uint32_t e = 0; ok; ++e) {
+            const uint32_t bt = e / BATCH, slot = bt % NBATCH;
+            if (e % BATCH == 0) {
+                if (!(ok = wait_warp(c, bar(L::bfull(slot)), (bt / NBATCH) & 1u))) break;
+                ptx::tc_fence_after();
+            }
+            const uint32_t s = e % NSTAGE;
+            const int4 h0 = hdr[2 * s], h1 = hdr[2 * s + 1];
+            const int flags = h0.z;
+            if (flags & F_TERM) break;
+            const int64_t item = (int64_t)(uint32_t)h1.z | ((int64_t)h1.w << 32);
+            if (flags & F_MMA) {
+                const int c0 = h0.x;
+                const uint32_t idesc = (uint32_t)h0.y;
+                const int ncols = (int)((idesc >> 17) & 0x3Fu) << 3;
+                const bool in_range = c0 >= 0 && c0 + ncols <= NB && ncols >= 16 && ncols <= NCAP &&
+                                      ((c0 | ncols) & 15) == 0;
+                if (!in_range) {
+                    if (lane == 0) atomicOr(err, ERRBIT_BOUNDS);
+                } else {
+                    const uint32_t mask = (uint32_t)h0.w;
+                    const uint32_t inc_lo = (uint32_t)h1.x, inc_hi = (uint32_t)h1.y;
+                    if (((cnt_lo + inc_lo) | (cnt_hi + inc_hi)) & flush4) {
+                        if (!(ok = close_segment(item, 0))) break;
+                        first = 0;
+                    }
+                    cnt_lo += inc_lo;
+                    cnt_hi += inc_hi;
+                    touched |= mask;
+                    const uint64_t so = (uint64_t)s * (STAGE_BYTES >> 4);
+                    mma3_elect(tmem + (uint32_t)(b * NB + c0), d_ahi + so, d_alo + so, d_bhi + so,
+                               d_blo + so, idesc);
+                }
+            }
+            if (flags & F_ITEM_END) {
+                if (!(ok = close_segment(item, 1))) break;
+                first = 1;
+            }
+            if (e % BATCH == BATCH - 1) commit_elect(bar(L::bempty(slot)));
         }
+        // every MMA issued has completed before the accumulator is released
+        commit_elect(bar(L::drain()));
+        drain_bar(bar(L::drain()), 0);
         __syncwarp();
     } else if (warp >= WARP_EPI0) {
         // ---------------------------------------------------------- epilogue
@@ -604,10 +753,12 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
         ptx::tc_fence_before();
         __syncwarp();
         if (lane == 0)
-            for (int b = 0; b < NACC; ++b) ptx::mbar_arrive(bar(L::aempty(b)));
+            for (int a = 0; a < NACC; ++a) ptx::mbar_arrive(bar(L::aempty(a)));
         bool ok = true;
         uint32_t seg = 0;
         const bool vec = (pl.gt & 3) == 0;
+        // A and B carry neither c_s nor c_t: both join the normalisation here
+        const float scale = pl.norm * (pl.cs * pl.ct);
         while (ok) {
             const int b = (int)(seg & 1u);
             const uint32_t par = (seg >> 1) & 1u;
@@ -645,10 +796,10 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                     }
 #pragma unroll
                     for (int v4 = 0; v4 < 8; ++v4) {
-                        float4 o = make_float4(__uint_as_float(r[4 * v4]) * pl.norm,
-                                               __uint_as_float(r[4 * v4 + 1]) * pl.norm,
-                                               __uint_as_float(r[4 * v4 + 2]) * pl.norm,
-                                               __uint_as_float(r[4 * v4 + 3]) * pl.norm);
+                        float4 o = make_float4(__uint_as_float(r[4 * v4]) * scale,
+                                               __uint_as_float(r[4 * v4 + 1]) * scale,
+                                               __uint_as_float(r[4 * v4 + 2]) * scale,
+                                               __uint_as_float(r[4 * v4 + 3]) * scale);
                         if (!first) {
                             o.x += pv[v4].x; o.y += pv[v4].y; o.z += pv[v4].z; o.w += pv[v4].w;
                         }
@@ -658,7 +809,7 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
 #pragma unroll
                     for (int jx = 0; jx < 32; ++jx) {
                         if (jx < nv) {
-                            float o = __uint_as_float(r[jx]) * pl.norm;
+                            float o = __uint_as_float(r[jx]) * scale;
                             if (!first) o += dst[col + jx];
                             dst[col + jx] = o;
                         }
@@ -699,9 +850,9 @@ bool launch_cfg(const Plan& pl, const Bins& b, float* out, int* err, cudaStream_
     const int64_t items = (int64_t)pl.ntx * pl.nty * ntb;
     if (items <= 0) return true;
     const int grid = (int)(items < sms ? items : sms);
-    // chunks (three accumulation steps each) per 32-column block before a segment
-    // is closed: bounds the round-toward-zero drift of the tensor-core
-    // accumulation per segment
+    // chunks (three accumulation steps each) per 32-column block at which a
+    // segment is closed (a power of two: the MMA warp tests it as a bit mask):
+    // bounds the round-toward-zero drift of the tensor-core accumulation per segment
     const int flush_chunks = FP16 ? 64 : 128;
     kern<<<grid, NTHREADS, L::TOTAL, st>>>(pl, b.ev, b.start, out, err, items, flush_chunks);
     return true;
