@@ -18,33 +18,38 @@
 // fixed number of chunks; the epilogue stores the first segment of a tile and
 // adds later ones to it in fp32 (round to nearest), which bounds the drift.
 //
-// Persistent CTA per SM, warp-specialised, every hand-off through mbarriers
-// (warp w runs on scheduler w % 4; the MMA warp shares its scheduler only with
-// the light loader and one epilogue warp):
-//   warp 0             MMA issue (the whole warp runs the loop, one elected
-//                      lane issues), tensor-memory allocation
-//   warp 4             loader: walks the tile's event bins and stages them, in
-//                      bin order, into 256-event shared-memory pages with
-//                      cp.async.bulk (no multicast), one copy per bin run, all
-//                      lanes issuing in parallel
-//   warps 1-3,5-7,9-11 nine generators.  Every generator reads every page; the
-//                      page's owner (page q: generator q mod 9) keeps the events
-//                      whose cylinder reaches the tile, compacting the page in
-//                      place, and records per chunk of 16 kept events the T
-//                      columns their windows cover.  Each chunk becomes one
-//                      "entry" per column window of up to 80 columns of a
-//                      CTA-wide sequence; entry e is built by generator e mod 9
-//                      into stage e mod 12 of a shared ring: A = K_s and B = K_t
-//                      as hi and lo 16-bit tiles in the tensor cores' shared
-//                      memory layout, handed to the MMA warp one stage at a time.
-//   warps 12-15        epilogue: one per tensor-memory lane quarter; scales by
-//                      c_s c_t / (n hs^2 ht), writes each voxel of the tile (vector
-//                      stores), adds later segments, zeroes the accumulator
-// Two accumulators of 256 columns let the epilogue of one segment overlap the
-// MMAs of the next.  The MMA warp consumes the entries strictly in sequence, so
-// every voxel sums its events in the same order on every run (bit-reproducible,
-// no global atomics).  The builder of the earliest unbuilt entry only waits on
-// earlier entries, so no wait can close a cycle.
+// Persistent CTA per SM holding two independent pipelines ("streams"), each
+// with its own loader, four generators, stage ring, MMA warp and 256-column
+// accumulator; the four epilogue warps serve both.  One MMA warp issues at most
+// one entry every few hundred cycles (stage wait, header, three MMAs, commit),
+// so two streams double the issue rate.  Tiles are handed to the streams on
+// demand (a shared counter over the CTA's tiles); each tile is computed by one
+// stream in a fixed order, so the result does not depend on which stream or CTA
+// computes it.  Roles (warp w runs on scheduler w % 4):
+//   warps 0, 8        MMA issue for streams 0, 1 (the whole warp runs the loop,
+//                     one elected lane issues); warp 0 allocates tensor memory
+//   warps 4, 11       loaders: walk a tile's event bins and stage them, in bin
+//                     order, into 256-event shared-memory pages with
+//                     cp.async.bulk (no multicast), one copy per bin run, all
+//                     lanes issuing in parallel; then, one page behind, keep the
+//                     events whose cylinder reaches the tile (compacting the page
+//                     in place) and record per chunk of 16 kept events the T
+//                     columns their windows cover, and the page's entry table
+//   warps 1-3,5       generators of stream 0; warps 6,7,9,10 of stream 1.
+//                     Every generator of a stream reads every page of it.  Each
+//                     chunk becomes one "entry" per column window of up to 80
+//                     columns; entry e of a stream is built by generator e mod 4
+//                     into stage e mod 6 of the stream's ring: A = K_s and
+//                     B = K_t as hi and lo 16-bit tiles in the tensor cores'
+//                     shared memory layout.
+//   warps 12-15       epilogue: one per tensor-memory lane quarter; scales by
+//                     c_s c_t / (n hs^2 ht), writes each voxel of the tile
+//                     (vector stores), adds later segments, zeroes the
+//                     accumulator.  It serves whichever stream has a segment
+//                     ready.
+// The builder of a stream's earliest unbuilt entry only waits on that stream's
+// earlier entries, and the streams share only the epilogue, which never waits on
+// a stream's producers, so no wait can close a cycle.
 //
 // Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
 // kernel sets the timeout bit of the error word, every role leaves its loop,
@@ -61,23 +66,19 @@ namespace stkde {
 
 namespace {
 
-constexpr int NB = 256;            // T columns per tile = accumulator width
-constexpr int NACC = 2;            // accumulators (512 tensor-memory columns)
-constexpr int NGEN = 9;            // generator warps
+constexpr int NSTREAM = 2;
+constexpr int NB = 256;            // T columns per tile = accumulator width per stream
+constexpr int NGEN = 4;            // generator warps per stream
 constexpr int NEPI = 4;            // epilogue warps
-constexpr int WARP_MMA = 0;
-constexpr int WARP_LOAD = 4;
 constexpr int WARP_EPI0 = 12;
 constexpr int NTHREADS = 16 * 32;
 constexpr int PAGE = 256;          // events per staging page
-constexpr int NPAGES = 6;
+constexpr int NPAGES = 5;          // pages per stream
 constexpr int CHUNK = 16;          // events per MMA (K of kind::f16)
 constexpr int MAXCH = PAGE / CHUNK;
 constexpr int MAXENT = 64;         // entries per page: 16 chunks x at most 4 windows
 constexpr int NCAP = 80;           // T columns per entry (one column window)
-constexpr int BATCH = 1;           // entries per hand-off to the MMA warp (measured best)
-constexpr int NBATCH = 12;
-constexpr int NSTAGE = BATCH * NBATCH;
+constexpr int NSTAGE = 6;          // stages per stream, handed over one at a time
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr uint64_t DRAIN_NS = 200000000ull;
 constexpr uint32_t A_BYTES = TILE_XY * CHUNK * 2;   // 4 KB
@@ -96,48 +97,57 @@ constexpr uint32_t TAB_BYTES = TAB_TK + 128;
 // entry header flags
 constexpr int F_MMA = 1;        // the stage holds operands for the MMA
 constexpr int F_ITEM_END = 4;   // last entry of a tile
-constexpr int F_TERM = 8;       // end of the CTA's sequence (and padding after it)
+constexpr int F_TERM = 8;       // end of the stream's sequence
 // page meta flags (written by the loader)
 constexpr int P_ITEM_END = 4;
 constexpr int P_TERM = 8;
+// segment descriptor flags (MMA warp -> epilogue)
+constexpr int D_FIRST = 1, D_LAST = 2, D_TERM = 4;
 
-// generator index of a warp (-1: not a generator)
-__device__ __forceinline__ int gen_index(int warp) {
-    return (warp >= 1 && warp <= 3) ? warp - 1 : (warp >= 5 && warp <= 7) ? warp - 2
-         : (warp >= 9 && warp <= 11) ? warp - 3 : -1;
+// roles
+__device__ __forceinline__ int mma_stream(int w) { return w == 0 ? 0 : w == 8 ? 1 : -1; }
+__device__ __forceinline__ int load_stream(int w) { return w == 4 ? 0 : w == 11 ? 1 : -1; }
+// generator id: stream * NGEN + index within the stream (-1: not a generator)
+__device__ __forceinline__ int gen_id(int w) {
+    return (w >= 1 && w <= 3) ? w - 1 : w == 5 ? 3 : (w == 6 || w == 7) ? w - 2
+         : (w == 9 || w == 10) ? w - 3 : -1;
 }
 
 struct L {
     static constexpr uint32_t OFF_STAGE = 0;
-    static constexpr uint32_t OFF_PAGES = OFF_STAGE + NSTAGE * STAGE_BYTES;
-    static constexpr uint32_t OFF_TAB = OFF_PAGES + NPAGES * PAGE * 16;
-    static constexpr uint32_t OFF_HDR = OFF_TAB + NGEN * TAB_BYTES;
-    static constexpr uint32_t OFF_PMETA = OFF_HDR + NSTAGE * 32;
-    static constexpr uint32_t OFF_KEPT = OFF_PMETA + NPAGES * 32;
-    static constexpr uint32_t OFF_CTAB = OFF_KEPT + NPAGES * 16;
-    static constexpr uint32_t OFF_ENT = OFF_CTAB + NPAGES * MAXCH * 8;
-    static constexpr uint32_t OFF_DESC = OFF_ENT + NPAGES * MAXENT * 2;
-    static constexpr uint32_t OFF_BAR = OFF_DESC + NACC * 16;
-    static constexpr int NBARS = 3 * NPAGES + 2 * NBATCH + 3 * NACC + 1;
-    static constexpr uint32_t OFF_MISC = OFF_BAR + NBARS * 8;
+    static constexpr uint32_t OFF_PAGES = OFF_STAGE + NSTREAM * NSTAGE * STAGE_BYTES;
+    static constexpr uint32_t OFF_TAB = OFF_PAGES + NSTREAM * NPAGES * PAGE * 16;
+    static constexpr uint32_t OFF_HDR = OFF_TAB + NSTREAM * NGEN * TAB_BYTES;
+    static constexpr uint32_t OFF_PMETA = OFF_HDR + NSTREAM * NSTAGE * 32;
+    static constexpr uint32_t OFF_KEPT = OFF_PMETA + NSTREAM * NPAGES * 32;
+    static constexpr uint32_t OFF_CTAB = OFF_KEPT + NSTREAM * NPAGES * 16;
+    static constexpr uint32_t OFF_ENT = OFF_CTAB + NSTREAM * NPAGES * MAXCH * 8;
+    static constexpr uint32_t OFF_DESC = OFF_ENT + NSTREAM * NPAGES * MAXENT * 2;
+    static constexpr uint32_t OFF_BAR = OFF_DESC + NSTREAM * 16;
+    static constexpr int BARS_PER_STREAM = 3 * NPAGES + 2 * NSTAGE + 4;
+    static constexpr int NBARS = NSTREAM * BARS_PER_STREAM;
+    static constexpr uint32_t OFF_MISC = OFF_BAR + NBARS * 8;  // tmem base, abort flag, tile counter
     static constexpr uint32_t TOTAL = OFF_MISC + 16;
-    __host__ __device__ static constexpr int pfull(int p) { return p; }
-    __host__ __device__ static constexpr int pempty(int p) { return NPAGES + p; }
-    __host__ __device__ static constexpr int pfilt(int p) { return 2 * NPAGES + p; }
-    __host__ __device__ static constexpr int bfull(int b) { return 3 * NPAGES + b; }
-    __host__ __device__ static constexpr int bempty(int b) { return 3 * NPAGES + NBATCH + b; }
-    __host__ __device__ static constexpr int afull(int a) { return 3 * NPAGES + 2 * NBATCH + a; }
-    __host__ __device__ static constexpr int aempty(int a) { return 3 * NPAGES + 2 * NBATCH + NACC + a; }
-    __host__ __device__ static constexpr int dfull(int a) { return 3 * NPAGES + 2 * NBATCH + 2 * NACC + a; }
-    __host__ __device__ static constexpr int drain() { return 3 * NPAGES + 2 * NBATCH + 3 * NACC; }
+    // barrier indices of stream p
+    __host__ __device__ static constexpr int pfull(int p, int q) { return p * BARS_PER_STREAM + q; }
+    __host__ __device__ static constexpr int pempty(int p, int q) { return p * BARS_PER_STREAM + NPAGES + q; }
+    __host__ __device__ static constexpr int pfilt(int p, int q) { return p * BARS_PER_STREAM + 2 * NPAGES + q; }
+    __host__ __device__ static constexpr int sfull(int p, int s) { return p * BARS_PER_STREAM + 3 * NPAGES + s; }
+    __host__ __device__ static constexpr int sempty(int p, int s) {
+        return p * BARS_PER_STREAM + 3 * NPAGES + NSTAGE + s;
+    }
+    __host__ __device__ static constexpr int afull(int p) { return p * BARS_PER_STREAM + 3 * NPAGES + 2 * NSTAGE; }
+    __host__ __device__ static constexpr int aempty(int p) { return afull(p) + 1; }
+    __host__ __device__ static constexpr int dfull(int p) { return afull(p) + 2; }
+    __host__ __device__ static constexpr int drain(int p) { return afull(p) + 3; }
     static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
     static_assert(TAB_BYTES % 16 == 0 && OFF_PAGES % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
     static_assert(TOTAL <= 227 * 1024, "shared memory budget");
     static_assert(NCAP % 16 == 0 && NCAP <= NB, "column window");
-    // a generator's consecutive entries are NGEN apart; for its stage waits to
-    // be at most one barrier phase behind, NGEN entries may span at most NBATCH
-    // batches
-    static_assert(NGEN <= BATCH * (NBATCH - 1) + 1, "stage ring too short for the generators");
+    static_assert(NSTREAM * NB <= 512, "tensor memory");
+    // a generator's consecutive entries are NGEN apart; its stage waits stay at
+    // most one barrier phase behind when NGEN <= NSTAGE
+    static_assert(NGEN <= NSTAGE, "stage ring too short for the generators");
 };
 
 __device__ __forceinline__ float2 fneg2(float2 a) { return make_float2(-a.x, -a.y); }
@@ -202,6 +212,15 @@ struct Ctl {
     int* err;
 };
 
+__device__ __forceinline__ bool timed_out(const Ctl& c, uint64_t t0) {
+    if (ptx::globaltimer() - t0 > WAIT_NS) {
+        *c.abort = 1;
+        atomicOr(c.err, ERRBIT_TIMEOUT);
+        return true;
+    }
+    return false;
+}
+
 // Bounded wait for the phase of parity `parity` of barrier `bar`.  Returns
 // false (and raises the abort flag) after WAIT_NS, or as soon as another role
 // has aborted.
@@ -212,11 +231,7 @@ __device__ __forceinline__ bool wait_bar(const Ctl& c, uint32_t bar, uint32_t pa
         if (ptx::mbar_try_wait(bar, parity)) return true;
         if ((it & 63) == 0) {
             if (*c.abort) return false;
-            if (ptx::globaltimer() - t0 > WAIT_NS) {
-                *c.abort = 1;
-                atomicOr(c.err, ERRBIT_TIMEOUT);
-                return false;
-            }
+            if (timed_out(c, t0)) return false;
         }
     }
 }
@@ -250,165 +265,61 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
     const uint32_t sb = ptx::smem_addr(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Ctl c{reinterpret_cast<volatile int*>(smem + L::OFF_MISC + 4), err};
+    int* next_tile = reinterpret_cast<int*>(smem + L::OFF_MISC + 8);
     auto bar = [sb](int i) -> uint32_t { return sb + L::OFF_BAR + 8u * (uint32_t)i; };
-    int4* pmeta = reinterpret_cast<int4*>(smem + L::OFF_PMETA);
-    int4* pkept = reinterpret_cast<int4*>(smem + L::OFF_KEPT);
-    int2* ctab = reinterpret_cast<int2*>(smem + L::OFF_CTAB);
-    uint16_t* pent = reinterpret_cast<uint16_t*>(smem + L::OFF_ENT);
+    int4* pmeta = reinterpret_cast<int4*>(smem + L::OFF_PMETA);   // [stream][page][2]
+    int4* pkept = reinterpret_cast<int4*>(smem + L::OFF_KEPT);    // [stream][page]
+    int2* ctab = reinterpret_cast<int2*>(smem + L::OFF_CTAB);     // [stream][page][chunk]
+    uint16_t* pent = reinterpret_cast<uint16_t*>(smem + L::OFF_ENT);  // [stream][page][entry]
 
     if (threadIdx.x == 0) {
-        for (int p = 0; p < NPAGES; ++p) {
-            ptx::mbar_init(bar(L::pfull(p)), 1);
-            ptx::mbar_init(bar(L::pempty(p)), NGEN);
-            ptx::mbar_init(bar(L::pfilt(p)), 1);
+        for (int p = 0; p < NSTREAM; ++p) {
+            for (int q = 0; q < NPAGES; ++q) {
+                ptx::mbar_init(bar(L::pfull(p, q)), 1);
+                ptx::mbar_init(bar(L::pempty(p, q)), NGEN);
+                ptx::mbar_init(bar(L::pfilt(p, q)), 1);
+            }
+            for (int s = 0; s < NSTAGE; ++s) {
+                ptx::mbar_init(bar(L::sfull(p, s)), 1);
+                ptx::mbar_init(bar(L::sempty(p, s)), 1);
+            }
+            ptx::mbar_init(bar(L::afull(p)), 1);
+            ptx::mbar_init(bar(L::aempty(p)), NEPI);
+            ptx::mbar_init(bar(L::dfull(p)), 1);
+            ptx::mbar_init(bar(L::drain(p)), 1);
         }
-        for (int b = 0; b < NBATCH; ++b) {
-            ptx::mbar_init(bar(L::bfull(b)), BATCH);
-            ptx::mbar_init(bar(L::bempty(b)), 1);
-        }
-        for (int a = 0; a < NACC; ++a) {
-            ptx::mbar_init(bar(L::afull(a)), 1);
-            ptx::mbar_init(bar(L::aempty(a)), NEPI);
-            ptx::mbar_init(bar(L::dfull(a)), 1);
-        }
-        ptx::mbar_init(bar(L::drain()), 1);
         *c.abort = 0;
+        *next_tile = 0;
         ptx::fence_mbar_init();
     }
-    if (warp == WARP_MMA) {
-        ptx::tmem_alloc(sb + L::OFF_MISC, NB * NACC);
+    if (warp == 0) {
+        ptx::tmem_alloc(sb + L::OFF_MISC, NB * NSTREAM);
         ptx::tmem_relinquish();
     }
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + L::OFF_MISC);
-    const int gi = gen_index(warp);
+    const int gid = gen_id(warp);
 
-    if (warp == WARP_LOAD) {
+    if (load_stream(warp) >= 0) {
         // ------------------------------------------------------------ loader
+        const int p = load_stream(warp);
         uint32_t pg = 0, fill = 0;
         bool open = false, ok = true;
         auto open_page = [&]() -> bool {
-            if (!wait_warp(c, bar(L::pempty(pg % NPAGES)), ((pg / NPAGES) & 1u) ^ 1u)) return false;
+            if (!wait_warp(c, bar(L::pempty(p, pg % NPAGES)), ((pg / NPAGES) & 1u) ^ 1u)) return false;
             open = true;
             fill = 0;
             return true;
         };
         // page meta: fill, flags, item, and the item's tile coordinates
-        auto close_page = [&](int flags, int64_t item, int tx, int ty, int tb) {
-            __syncwarp();
-            if (lane == 0) {
-                const uint32_t p = pg % NPAGES;
-                pmeta[2 * p] = make_int4((int)fill, flags, (int)(item & 0xffffffff), (int)(item >> 32));
-                pmeta[2 * p + 1] = make_int4(tx, ty, tb, 0);
-                ptx::mbar_arrive(bar(L::pfull(p)));
-            }
-            __syncwarp();
-            ++pg;
-            open = false;
-        };
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-            int tx, ty, tb;
-            decode_item(pl, item, tx, ty, tb);
-            const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
-            const int ncx = g.cx_hi - g.cx_lo + 1;
-            const int nr = (g.s_hi >= g.s_lo && ncx > 0) ? (g.s_hi - g.s_lo + 1) * ncx : 0;
-            for (int r0 = 0; r0 < nr && ok; r0 += 32) {
-                // 32 bin runs at a time: lane-parallel lengths, offsets by a warp scan
-                uint32_t a = 0, len = 0;
-                const int r = r0 + lane;
-                if (r < nr) {
-                    const int s = g.s_lo + r / ncx, cx = g.cx_lo + r % ncx;
-                    const uint32_t kb =
-                        ((uint32_t)s * (uint32_t)pl.ntx + (uint32_t)cx) * (uint32_t)pl.nty;
-                    a = start[kb + g.cy_lo];
-                    len = start[kb + g.cy_hi + 1] - a;
-                }
-                uint32_t incl = len;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const uint32_t off = incl - len, tot = __shfl_sync(0xffffffffu, incl, 31);
-                uint32_t done = 0;
-                while (done < tot) {
-                    if (!open && !(ok = open_page())) break;
-                    const uint32_t p = pg % NPAGES;
-                    const uint32_t take = min((uint32_t)PAGE - fill, tot - done);
-                    // this page takes pass positions [done, done + take); each lane copies
-                    // the part of its own run that falls there
-                    const uint32_t lo = max(off, done), hi = min(off + len, done + take);
-                    if (hi > lo) {
-                        ptx::mbar_expect_tx(bar(L::pfull(p)), (hi - lo) * 16u);
-                        ptx::bulk_g2s(sb + L::OFF_PAGES + (p * PAGE + fill + (lo - done)) * 16u,
-                                      ev + a + (lo - off), (hi - lo) * 16u, bar(L::pfull(p)));
-                    }
-                    fill += take;
-                    done += take;
-                    if (fill == (uint32_t)PAGE) close_page(0, item, tx, ty, tb);
-                }
-            }
-            if (!ok) break;
-            if (!open && !(ok = open_page())) break;
-            close_page(P_ITEM_END, item, tx, ty, tb);  // the tile's last page, possibly empty
-        }
-        // termination page (every generator reads every page)
-        if (ok && (ok = open_page())) close_page(P_TERM, 0, 0, 0, 0);
-        if (!ok) {
-            if (open) close_page(P_TERM, 0, 0, 0, 0);
-            for (uint32_t q = (pg > NPAGES ? pg - NPAGES : 0); q < pg; ++q)
-                drain_bar(bar(L::pfull(q % NPAGES)), (q / NPAGES) & 1u);
-        }
-    } else if (gi >= 0) {
-        // -------------------------------------------------------- generators
-        uint8_t* tab = smem + L::OFF_TAB + gi * TAB_BYTES;
-        float* xa = reinterpret_cast<float*>(tab + TAB_XA);
-        float* yb = reinterpret_cast<float*>(tab + TAB_YB);
-        float* tkt = reinterpret_cast<float*>(tab + TAB_TK);
+        // Keeps the events of page fq (staged by this loader) whose cylinder
+        // reaches their tile, compacted in place; records per chunk the covered
+        // columns and the page's entry table; publishes the kept and entry counts.
         const uint32_t lt = (1u << lane) - 1u;
-        const float inv_hs = pl.inv_hs, inv_ht = pl.inv_ht;
-        const uint32_t fmt = FP16 ? 0u : 1u;
-        bool ok = true;
-        uint32_t ebase = 0;  // sequence entries before the current page
-        uint32_t emod = 0;   // ebase mod NGEN
-
-        // waits until entry e's stage is free (its previous batch consumed)
-        auto slot_wait = [&](uint32_t e) -> bool {
-            const uint32_t bt = e / BATCH, use = bt / NBATCH;
-            if (use == 0) return true;
-            return wait_warp(c, bar(L::bempty(bt % NBATCH)), (use - 1u) & 1u);
-        };
-        // hands entry e to the MMA warp, with what it needs precomputed: the
-        // instruction descriptor, the 32-column blocks the MMAs touch and the
-        // per-block chunk-count increments (bytes, four blocks per word)
-        auto publish = [&](uint32_t e, int c0, int ncols, int flags, int64_t item) {
-            const uint32_t s = e % NSTAGE;
-            if (lane == 0) {
-                uint32_t idesc = 0, mask = 0, inc_lo = 0, inc_hi = 0;
-                if (flags & F_MMA) {
-                    idesc = ptx::idesc_f16(128, (uint32_t)ncols, fmt);
-                    const uint32_t b0 = (uint32_t)c0 >> 5, b1 = (uint32_t)(c0 + ncols - 1) >> 5;
-                    mask = ((2u << b1) - 1u) & ~((1u << b0) - 1u);
-                    inc_lo = ((mask & 15u) * 0x204081u) & 0x01010101u;
-                    inc_hi = ((mask >> 4) * 0x204081u) & 0x01010101u;
-                }
-                int4* h = reinterpret_cast<int4*>(smem + L::OFF_HDR + s * 32);
-                h[0] = make_int4(c0, (int)idesc, flags, (int)mask);
-                h[1] = make_int4((int)inc_lo, (int)inc_hi, (int)(item & 0xffffffff), (int)(item >> 32));
-            }
-            ptx::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(bar(L::bfull((e / BATCH) % NBATCH)));
-        };
-        // Keeps the events of page fq (staged, owned by this generator) whose
-        // cylinder reaches their tile, compacted in place; records per chunk the
-        // covered columns and the chunk's first sequence entry; publishes the
-        // kept and entry counts.
-        uint32_t filt_next = (uint32_t)gi;  // next owned page not yet filtered
         auto filter_page = [&](uint32_t fq) {
-            const uint32_t fp = fq % NPAGES;
+            const uint32_t fp = p * NPAGES + fq % NPAGES;
             float4* fb = reinterpret_cast<float4*>(smem + L::OFF_PAGES + fp * PAGE * 16);
             int2* ct = ctab + fp * MAXCH;
             uint16_t* ent = pent + fp * MAXENT;
@@ -483,51 +394,155 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             __syncwarp();
             if (lane == 0) {
                 pkept[fp] = make_int4((int)kept, (int)nent, 0, 0);
-                ptx::mbar_arrive(bar(L::pfilt(fp)));
+                ptx::mbar_arrive(bar(L::pfilt(p, fq % NPAGES)));
             }
             __syncwarp();
-            filt_next = fq + NGEN;
         };
-        // filters the next owned page ahead of time if it is already staged
-        auto filter_ahead = [&](uint32_t q) {
-            if (filt_next > q && filt_next < q + NPAGES) {
-                const uint32_t fp = filt_next % NPAGES;
-                const bool ready = __all_sync(0xffffffffu,
-                    ptx::mbar_try_wait(bar(L::pfull(fp)), (filt_next / NPAGES) & 1u));
-                if (ready) filter_page(filt_next);
+        // filters the page staged before the last one closed: its copies have had
+        // the time of a page fill to land
+        uint32_t nfilt = 0;  // pages filtered so far
+        auto filter_upto = [&](uint32_t lim) -> bool {
+            for (; nfilt < lim; ++nfilt) {
+                if (!wait_warp(c, bar(L::pfull(p, nfilt % NPAGES)), (nfilt / NPAGES) & 1u)) return false;
+                filter_page(nfilt);
             }
+            return true;
+        };
+        auto close_page = [&](int flags, int64_t item, int tx, int ty, int tb) {
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t q = p * NPAGES + pg % NPAGES;
+                pmeta[2 * q] = make_int4((int)fill, flags, (int)(item & 0xffffffff), (int)(item >> 32));
+                pmeta[2 * q + 1] = make_int4(tx, ty, tb, 0);
+                ptx::mbar_arrive(bar(L::pfull(p, pg % NPAGES)));
+            }
+            __syncwarp();
+            ++pg;
+            open = false;
+            if (!(flags & P_TERM)) ok = ok && filter_upto(pg - 1);
+        };
+        while (ok) {
+            // the CTA's tiles are blockIdx.x + k * gridDim.x; take the next k
+            int k = 0;
+            if (lane == 0) k = atomicAdd(next_tile, 1);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            const int64_t item = (int64_t)blockIdx.x + (int64_t)k * gridDim.x;
+            if (item >= nitems) break;
+            int tx, ty, tb;
+            decode_item(pl, item, tx, ty, tb);
+            const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
+            const int ncx = g.cx_hi - g.cx_lo + 1;
+            const int nr = (g.s_hi >= g.s_lo && ncx > 0) ? (g.s_hi - g.s_lo + 1) * ncx : 0;
+            for (int r0 = 0; r0 < nr && ok; r0 += 32) {
+                // 32 bin runs at a time: lane-parallel lengths, offsets by a warp scan
+                uint32_t a = 0, len = 0;
+                const int r = r0 + lane;
+                if (r < nr) {
+                    const int s = g.s_lo + r / ncx, cx = g.cx_lo + r % ncx;
+                    const uint32_t kb =
+                        ((uint32_t)s * (uint32_t)pl.ntx + (uint32_t)cx) * (uint32_t)pl.nty;
+                    a = start[kb + g.cy_lo];
+                    len = start[kb + g.cy_hi + 1] - a;
+                }
+                uint32_t incl = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const uint32_t off = incl - len, tot = __shfl_sync(0xffffffffu, incl, 31);
+                uint32_t done = 0;
+                while (done < tot) {
+                    if (!open && !(ok = open_page())) break;
+                    const uint32_t q = p * NPAGES + pg % NPAGES;
+                    const uint32_t take = min((uint32_t)PAGE - fill, tot - done);
+                    // this page takes pass positions [done, done + take); each lane copies
+                    // the part of its own run that falls there
+                    const uint32_t lo = max(off, done), hi = min(off + len, done + take);
+                    if (hi > lo) {
+                        ptx::mbar_expect_tx(bar(L::pfull(p, pg % NPAGES)), (hi - lo) * 16u);
+                        ptx::bulk_g2s(sb + L::OFF_PAGES + (q * PAGE + fill + (lo - done)) * 16u,
+                                      ev + a + (lo - off), (hi - lo) * 16u, bar(L::pfull(p, pg % NPAGES)));
+                    }
+                    fill += take;
+                    done += take;
+                    if (fill == (uint32_t)PAGE) close_page(0, item, tx, ty, tb);
+                }
+            }
+            if (!ok) break;
+            if (!open && !(ok = open_page())) break;
+            close_page(P_ITEM_END, item, tx, ty, tb);  // the tile's last page, possibly empty
+        }
+        // termination page (every generator of the stream reads every page)
+        if (ok) ok = filter_upto(pg);
+        if (ok && (ok = open_page())) close_page(P_TERM, 0, 0, 0, 0);
+        if (!ok) {
+            if (open) close_page(P_TERM, 0, 0, 0, 0);
+            for (uint32_t q = (pg > NPAGES ? pg - NPAGES : 0); q < pg; ++q)
+                drain_bar(bar(L::pfull(p, q % NPAGES)), (q / NPAGES) & 1u);
+        }
+    } else if (gid >= 0) {
+        // -------------------------------------------------------- generators
+        const int p = gid / NGEN, gi = gid % NGEN;
+        uint8_t* tab = smem + L::OFF_TAB + gid * TAB_BYTES;
+        float* xa = reinterpret_cast<float*>(tab + TAB_XA);
+        float* yb = reinterpret_cast<float*>(tab + TAB_YB);
+        float* tkt = reinterpret_cast<float*>(tab + TAB_TK);
+        const float inv_hs = pl.inv_hs, inv_ht = pl.inv_ht;
+        const uint32_t fmt = FP16 ? 0u : 1u;
+        bool ok = true;
+        uint32_t ebase = 0;  // the stream's entries before the current page
+        uint32_t emod = 0;   // ebase mod NGEN
+
+        // waits until entry e's stage is free (its previous entry consumed)
+        auto slot_wait = [&](uint32_t e) -> bool {
+            const uint32_t use = e / NSTAGE;
+            if (use == 0) return true;
+            return wait_warp(c, bar(L::sempty(p, e % NSTAGE)), (use - 1u) & 1u);
+        };
+        // hands entry e to the stream's MMA warp, with what it needs precomputed:
+        // the instruction descriptor, the 32-column blocks the MMAs touch and the
+        // per-block chunk-count increments (bytes, four blocks per word)
+        auto publish = [&](uint32_t e, int c0, int ncols, int flags, int64_t item) {
+            const uint32_t s = e % NSTAGE;
+            if (lane == 0) {
+                uint32_t idesc = 0, mask = 0, inc_lo = 0, inc_hi = 0;
+                if (flags & F_MMA) {
+                    idesc = ptx::idesc_f16(128, (uint32_t)ncols, fmt);
+                    const uint32_t b0 = (uint32_t)c0 >> 5, b1 = (uint32_t)(c0 + ncols - 1) >> 5;
+                    mask = ((2u << b1) - 1u) & ~((1u << b0) - 1u);
+                    inc_lo = ((mask & 15u) * 0x204081u) & 0x01010101u;
+                    inc_hi = ((mask >> 4) * 0x204081u) & 0x01010101u;
+                }
+                int4* h = reinterpret_cast<int4*>(smem + L::OFF_HDR + (p * NSTAGE + s) * 32);
+                h[0] = make_int4(c0, (int)idesc, flags, (int)mask);
+                h[1] = make_int4((int)inc_lo, (int)inc_hi, (int)(item & 0xffffffff), (int)(item >> 32));
+            }
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(bar(L::sfull(p, s)));
         };
         for (uint32_t q = 0; ok; ++q) {
-            const uint32_t p = q % NPAGES;
+            const uint32_t pq = p * NPAGES + q % NPAGES;
             const uint32_t ph = (q / NPAGES) & 1u;
-            const float4* page = reinterpret_cast<const float4*>(smem + L::OFF_PAGES + p * PAGE * 16);
-            if (!(ok = wait_warp(c, bar(L::pfull(p)), ph))) break;
-            const int4 meta = pmeta[2 * p], mt = pmeta[2 * p + 1];
+            const float4* page = reinterpret_cast<const float4*>(smem + L::OFF_PAGES + pq * PAGE * 16);
+            if (!(ok = wait_warp(c, bar(L::pfull(p, q % NPAGES)), ph))) break;
+            const int4 meta = pmeta[2 * pq], mt = pmeta[2 * pq + 1];
             if (meta.y & P_TERM) {
-                // the sequence ends with entry ebase; entries to the end of its batch are padding
-                const uint32_t eend = (ebase / BATCH + 1u) * BATCH;
-                for (uint32_t e = ebase; e < eend && ok; ++e) {
-                    if (e % NGEN != (uint32_t)gi) continue;
-                    if (!(ok = slot_wait(e))) break;
-                    publish(e, 0, 0, F_TERM, 0);
-                }
+                // the stream's sequence ends with entry ebase
+                if (ebase % NGEN == (uint32_t)gi && (ok = slot_wait(ebase))) publish(ebase, 0, 0, F_TERM, 0);
                 break;
             }
             const int64_t item = (int64_t)(uint32_t)meta.z | ((int64_t)meta.w << 32);
             const int end = meta.y & P_ITEM_END;
             const int X0 = mt.x * TX, Y0 = mt.y * TY, T0 = mt.z * NB;
-            if ((int)(q % NGEN) == gi && q >= filt_next) {
-                // this generator owns page q and has not filtered it ahead: do it now
-                filter_page(q);
-            } else if (!(ok = wait_warp(c, bar(L::pfilt(p)), ph))) {
-                break;
-            }
-            const int4 ki = pkept[p];
+            if (!(ok = wait_warp(c, bar(L::pfilt(p, q % NPAGES)), ph))) break;
+            const int4 ki = pkept[pq];
             const int kept = ki.x;
             const uint32_t nent = (uint32_t)ki.y;
             const int nch = (kept + CHUNK - 1) / CHUNK;
-            const int2* ct = ctab + p * MAXCH;
-            const uint16_t* ent = pent + p * MAXENT;
+            const int2* ct = ctab + pq * MAXCH;
+            const uint16_t* ent = pent + pq * MAXENT;
             // entry e is always built by generator e mod NGEN, so each generator's
             // entries are exactly NGEN apart and its stage waits are never more
             // than one barrier phase behind
@@ -544,7 +559,6 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                 const int2 cinfo = ct[ch];
                 const int nw = cinfo.y >> 16;
                 const int c0 = cinfo.x & 0xffff, cend = cinfo.x >> 16;
-                filter_ahead(q);
                 const int count = min(CHUNK, kept - ch * CHUNK);
 
                 // factor tables of K_s for the chunk's 16 events (missing events
@@ -569,210 +583,225 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                     yb[y * YB_STRIDE + k] = 1.0f - vv;
                     yb[y * YB_STRIDE + 16 + k] = vv;
                 }
-                {
-                    const int cw = c0 + w * NCAP;
-                    const int ncols = min(NCAP, cend - cw);
-                    // event time relative to the window's first voxel centre
-                    if (lane < CHUNK)
-                        tkt[lane] = real ? ek.z - ((float)(T0 + cw) + 0.5f) : 1.0e9f;
-                    __syncwarp();
-                    if (!(ok = slot_wait(e))) break;
-                    uint8_t* st = smem + L::OFF_STAGE + (e % NSTAGE) * STAGE_BYTES;
+                const int cw = c0 + w * NCAP;
+                const int ncols = min(NCAP, cend - cw);
+                // event time relative to the window's first voxel centre
+                if (lane < CHUNK) tkt[lane] = real ? ek.z - ((float)(T0 + cw) + 0.5f) : 1.0e9f;
+                __syncwarp();
+                if (!(ok = slot_wait(e))) break;
+                uint8_t* st = smem + L::OFF_STAGE + (p * NSTAGE + e % NSTAGE) * STAGE_BYTES;
 
-                    // A = K_s without c_s: row r = voxel (x = r / 8, y = r % 8); lane
-                    // owns rows lane + 32 j, all with y = lane % 8.  The disk test
-                    // (u^2 + v^2 < 1, i.e. (1 - u^2) - v^2 > 0) masks both halves.
-                    {
-                        const float* yrow = yb + (lane & 7) * YB_STRIDE;
-                        float2 bq[8], vq[8];
+                // A = K_s without c_s: row r = voxel (x = r / 8, y = r % 8); lane
+                // owns rows lane + 32 j, all with y = lane % 8.  The disk test
+                // (u^2 + v^2 < 1, i.e. (1 - u^2) - v^2 > 0) masks both halves.
+                {
+                    const float* yrow = yb + (lane & 7) * YB_STRIDE;
+                    float2 bq[8], vq[8];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 tb4 = *reinterpret_cast<const float4*>(yrow + 4 * i);
+                        const float4 tv4 = *reinterpret_cast<const float4*>(yrow + 16 + 4 * i);
+                        bq[2 * i] = make_float2(tb4.x, tb4.y);
+                        bq[2 * i + 1] = make_float2(tb4.z, tb4.w);
+                        vq[2 * i] = make_float2(tv4.x, tv4.y);
+                        vq[2 * i + 1] = make_float2(tv4.z, tv4.w);
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const float* xrow = xa + ((lane >> 3) + 4 * jj) * XA_STRIDE;
+                        uint32_t ah[8], al[8];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const float4 tb4 = *reinterpret_cast<const float4*>(yrow + 4 * i);
-                            const float4 tv4 = *reinterpret_cast<const float4*>(yrow + 16 + 4 * i);
-                            bq[2 * i] = make_float2(tb4.x, tb4.y);
-                            bq[2 * i + 1] = make_float2(tb4.z, tb4.w);
-                            vq[2 * i] = make_float2(tv4.x, tv4.y);
-                            vq[2 * i + 1] = make_float2(tv4.z, tv4.w);
-                        }
+                            const float4 t4 = *reinterpret_cast<const float4*>(xrow + 4 * i);
+                            const float2 aq[2] = {make_float2(t4.x, t4.y), make_float2(t4.z, t4.w)};
 #pragma unroll
-                        for (int jj = 0; jj < 4; ++jj) {
-                            const float* xrow = xa + ((lane >> 3) + 4 * jj) * XA_STRIDE;
-                            uint32_t ah[8], al[8];
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                const float4 t4 = *reinterpret_cast<const float4*>(xrow + 4 * i);
-                                const float2 aq[2] = {make_float2(t4.x, t4.y), make_float2(t4.z, t4.w)};
-#pragma unroll
-                                for (int h = 0; h < 2; ++h) {
-                                    const int pp = 2 * i + h;
-                                    const float2 pr = __fmul2_rn(aq[h], bq[pp]);
-                                    const float2 d = __fadd2_rn(aq[h], fneg2(vq[pp]));
-                                    split_rn<FP16>(pr, ah[pp], al[pp]);
-                                    const uint32_t m = sign_mask2(d.x, d.y);
-                                    ah[pp] &= ~m;
-                                    al[pp] &= ~m;
-                                }
+                            for (int h = 0; h < 2; ++h) {
+                                const int pp = 2 * i + h;
+                                const float2 pr = __fmul2_rn(aq[h], bq[pp]);
+                                const float2 d = __fadd2_rn(aq[h], fneg2(vq[pp]));
+                                split_rn<FP16>(pr, ah[pp], al[pp]);
+                                const uint32_t m = sign_mask2(d.x, d.y);
+                                ah[pp] &= ~m;
+                                al[pp] &= ~m;
                             }
-                            const int r = lane + 32 * jj;
-                            const uint32_t off = (uint32_t)(r >> 3) * CORE_SBO + (uint32_t)(r & 7) * 16;
-                            *reinterpret_cast<uint4*>(st + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
-                            *reinterpret_cast<uint4*>(st + off + CORE_LBO) = make_uint4(ah[4], ah[5], ah[6], ah[7]);
-                            *reinterpret_cast<uint4*>(st + A_BYTES + off) = make_uint4(al[0], al[1], al[2], al[3]);
-                            *reinterpret_cast<uint4*>(st + A_BYTES + off + CORE_LBO) =
-                                make_uint4(al[4], al[5], al[6], al[7]);
                         }
+                        const int r = lane + 32 * jj;
+                        const uint32_t off = (uint32_t)(r >> 3) * CORE_SBO + (uint32_t)(r & 7) * 16;
+                        *reinterpret_cast<uint4*>(st + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
+                        *reinterpret_cast<uint4*>(st + off + CORE_LBO) = make_uint4(ah[4], ah[5], ah[6], ah[7]);
+                        *reinterpret_cast<uint4*>(st + A_BYTES + off) = make_uint4(al[0], al[1], al[2], al[3]);
+                        *reinterpret_cast<uint4*>(st + A_BYTES + off + CORE_LBO) =
+                            make_uint4(al[4], al[5], al[6], al[7]);
                     }
-                    // B = K_t without c_t: (1 - w^2)_+ for the window's columns
-                    {
-                        float2 tq[8];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float4 t4 = *reinterpret_cast<const float4*>(tkt + 4 * i);
-                            tq[2 * i] = make_float2(-t4.x, -t4.y);
-                            tq[2 * i + 1] = make_float2(-t4.z, -t4.w);
-                        }
-                        const float2 ih2 = make_float2(inv_ht, inv_ht), one2 = make_float2(1.0f, 1.0f);
-                        uint8_t* bh = st + 2 * A_BYTES;
-                        uint8_t* bl = bh + B_BYTES;
-                        for (int n = lane; n < ncols; n += 32) {
-                            const float2 n2 = make_float2((float)n, (float)n);
-                            uint32_t h[8], l[8];
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                const float2 wv = __fmul2_rn(__fadd2_rn(n2, tq[i]), ih2);
-                                const float2 kt = __ffma2_rn(fneg2(wv), wv, one2);
-                                split_rn<FP16>(make_float2(fmaxf(kt.x, 0.0f), fmaxf(kt.y, 0.0f)), h[i], l[i]);
-                            }
-                            const uint32_t off = (uint32_t)(n >> 3) * CORE_SBO + (uint32_t)(n & 7) * 16;
-                            *reinterpret_cast<uint4*>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
-                            *reinterpret_cast<uint4*>(bh + off + CORE_LBO) = make_uint4(h[4], h[5], h[6], h[7]);
-                            *reinterpret_cast<uint4*>(bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
-                            *reinterpret_cast<uint4*>(bl + off + CORE_LBO) = make_uint4(l[4], l[5], l[6], l[7]);
-                        }
-                    }
-                    const int fl = F_MMA | ((end && ch == nch - 1 && w + 1 == nw) ? F_ITEM_END : 0);
-                    publish(e, cw, ncols, fl, item);
                 }
+                // B = K_t without c_t: (1 - w^2)_+ for the window's columns
+                {
+                    float2 tq[8];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 t4 = *reinterpret_cast<const float4*>(tkt + 4 * i);
+                        tq[2 * i] = make_float2(-t4.x, -t4.y);
+                        tq[2 * i + 1] = make_float2(-t4.z, -t4.w);
+                    }
+                    const float2 ih2 = make_float2(inv_ht, inv_ht), one2 = make_float2(1.0f, 1.0f);
+                    uint8_t* bh = st + 2 * A_BYTES;
+                    uint8_t* bl = bh + B_BYTES;
+                    for (int n = lane; n < ncols; n += 32) {
+                        const float2 n2 = make_float2((float)n, (float)n);
+                        uint32_t h[8], l[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float2 wv = __fmul2_rn(__fadd2_rn(n2, tq[i]), ih2);
+                            const float2 kt = __ffma2_rn(fneg2(wv), wv, one2);
+                            split_rn<FP16>(make_float2(fmaxf(kt.x, 0.0f), fmaxf(kt.y, 0.0f)), h[i], l[i]);
+                        }
+                        const uint32_t off = (uint32_t)(n >> 3) * CORE_SBO + (uint32_t)(n & 7) * 16;
+                        *reinterpret_cast<uint4*>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                        *reinterpret_cast<uint4*>(bh + off + CORE_LBO) = make_uint4(h[4], h[5], h[6], h[7]);
+                        *reinterpret_cast<uint4*>(bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                        *reinterpret_cast<uint4*>(bl + off + CORE_LBO) = make_uint4(l[4], l[5], l[6], l[7]);
+                    }
+                }
+                const int fl = F_MMA | ((end && ch == nch - 1 && w + 1 == nw) ? F_ITEM_END : 0);
+                publish(e, cw, ncols, fl, item);
             }
             if (!ok) break;
             // done with the page (only read here; the owner fenced its compaction)
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(bar(L::pempty(p)));
+            if (lane == 0) ptx::mbar_arrive(bar(L::pempty(p, q % NPAGES)));
             ebase += nent;
             emod = (emod + nent) % NGEN;
         }
-    } else if (warp == WARP_MMA) {
+    } else if (mma_stream(warp) >= 0) {
         // --------------------------------------------------------------- MMA
         // The whole warp runs the loop (converged); one elected lane issues.
+        const int p = mma_stream(warp);
+        const uint32_t acc = tmem + (uint32_t)(p * NB);
         uint32_t nseg = 0;  // accumulator segments closed so far
         bool ok = true;
-        // descriptors of stage 0; stage s adds s * STAGE_BYTES / 16 to the address field
-        const uint64_t d_ahi = ptx::smem_desc(sb + L::OFF_STAGE, CORE_LBO, CORE_SBO);
+        // descriptors of the stream's stage 0; stage s adds s * STAGE_BYTES / 16
+        const uint64_t d_ahi = ptx::smem_desc(sb + L::OFF_STAGE + p * NSTAGE * STAGE_BYTES, CORE_LBO, CORE_SBO);
         const uint64_t d_alo = d_ahi + (A_BYTES >> 4);
         const uint64_t d_bhi = d_ahi + ((2 * A_BYTES) >> 4);
         const uint64_t d_blo = d_ahi + ((2 * A_BYTES + B_BYTES) >> 4);
         // chunks per 32-column block at which a segment is closed (a power of
         // two below 128), as a bit mask over the four byte counters of a word
         const uint32_t flush4 = (uint32_t)flush_chunks * 0x01010101u;
-        const int4* hdr = reinterpret_cast<const int4*>(smem + L::OFF_HDR);
-        int b = 0;
+        const int4* hdr = reinterpret_cast<const int4*>(smem + L::OFF_HDR + p * NSTAGE * 32);
+        int4* desc = reinterpret_cast<int4*>(smem + L::OFF_DESC + p * 16);
         int first = 1;
         uint32_t touched = 0;             // 32-column blocks written in this segment
         uint32_t cnt_lo = 0, cnt_hi = 0;  // chunks per 32-column block (bytes)
-        // hands the current segment to the epilogue and opens the next one
-        auto close_segment = [&](int64_t item, int last) -> bool {
+        // hands the current segment to the epilogue and waits until it has been
+        // drained (this stream has one accumulator)
+        auto close_segment = [&](int64_t item, int flags) -> bool {
             if (lane == 0) {
-                ptx::sts_i4(sb + L::OFF_DESC + b * 16,
-                            make_int4((int)(item & 0xffffffff), (int)(item >> 32), first | (last ? 2 : 0),
-                                      (int)touched));
-                ptx::mbar_arrive(bar(L::dfull(b)));
+                *desc = make_int4((int)(item & 0xffffffff), (int)(item >> 32), flags, (int)touched);
+                ptx::mbar_arrive(bar(L::dfull(p)));
             }
             __syncwarp();
-            commit_elect(bar(L::afull(b)));
+            commit_elect(bar(L::afull(p)));
             ++nseg;
-            b = (int)(nseg & 1u);
-            if (!wait_warp(c, bar(L::aempty(b)), (nseg >> 1) & 1u)) return false;
+            if (flags & D_TERM) return true;
+            if (!wait_warp(c, bar(L::aempty(p)), nseg & 1u)) return false;
             ptx::tc_fence_after();
             touched = 0;
             cnt_lo = 0;
             cnt_hi = 0;
             return true;
         };
-        ok = wait_warp(c, bar(L::aempty(0)), 0);
+        ok = wait_warp(c, bar(L::aempty(p)), 0);
         ptx::tc_fence_after();
         for (uint32_t e = 0; ok; ++e) {
-            const uint32_t bt = e / BATCH, slot = bt % NBATCH;
-            if (e % BATCH == 0) {
-                if (!(ok = wait_warp(c, bar(L::bfull(slot)), (bt / NBATCH) & 1u))) break;
-                ptx::tc_fence_after();
-            }
             const uint32_t s = e % NSTAGE;
+            if (!(ok = wait_warp(c, bar(L::sfull(p, s)), (e / NSTAGE) & 1u))) break;
+            ptx::tc_fence_after();
             const int4 h0 = hdr[2 * s], h1 = hdr[2 * s + 1];
             const int flags = h0.z;
-            if (flags & F_TERM) break;
+            if (flags & F_TERM) {
+                close_segment(0, D_TERM);
+                break;
+            }
             const int64_t item = (int64_t)(uint32_t)h1.z | ((int64_t)h1.w << 32);
             if (flags & F_MMA) {
                 const int c0 = h0.x;
                 const uint32_t idesc = (uint32_t)h0.y;
                 const int ncols = (int)((idesc >> 17) & 0x3Fu) << 3;
+                // never issue an MMA outside the accumulator
                 const bool in_range = c0 >= 0 && c0 + ncols <= NB && ncols >= 16 && ncols <= NCAP &&
                                       ((c0 | ncols) & 15) == 0;
                 if (!in_range) {
                     if (lane == 0) atomicOr(err, ERRBIT_BOUNDS);
                 } else {
-                    const uint32_t mask = (uint32_t)h0.w;
                     const uint32_t inc_lo = (uint32_t)h1.x, inc_hi = (uint32_t)h1.y;
+                    // a byte (chunk count of one 32-column block) reaching the
+                    // power-of-two flush count closes the segment first
                     if (((cnt_lo + inc_lo) | (cnt_hi + inc_hi)) & flush4) {
-                        if (!(ok = close_segment(item, 0))) break;
+                        // close the segment: the epilogue adds it in fp32
+                        if (!(ok = close_segment(item, first ? D_FIRST : 0))) break;
                         first = 0;
                     }
                     cnt_lo += inc_lo;
                     cnt_hi += inc_hi;
-                    touched |= mask;
+                    touched |= (uint32_t)h0.w;
                     const uint64_t so = (uint64_t)s * (STAGE_BYTES >> 4);
-                    mma3_elect(tmem + (uint32_t)(b * NB + c0), d_ahi + so, d_alo + so, d_bhi + so,
-                               d_blo + so, idesc);
+                    mma3_elect(acc + (uint32_t)c0, d_ahi + so, d_alo + so, d_bhi + so, d_blo + so, idesc);
                 }
             }
             if (flags & F_ITEM_END) {
-                if (!(ok = close_segment(item, 1))) break;
+                if (!(ok = close_segment(item, (first ? D_FIRST : 0) | D_LAST))) break;
                 first = 1;
             }
-            if (e % BATCH == BATCH - 1) commit_elect(bar(L::bempty(slot)));
+            commit_elect(bar(L::sempty(p, s)));
         }
         // every MMA issued has completed before the accumulator is released
-        commit_elect(bar(L::drain()));
-        drain_bar(bar(L::drain()), 0);
+        commit_elect(bar(L::drain(p)));
+        drain_bar(bar(L::drain(p)), 0);
         __syncwarp();
     } else if (warp >= WARP_EPI0) {
         // ---------------------------------------------------------- epilogue
-        const int q = warp & 3;
-        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
-        for (int col = 0; col < NB * NACC; col += 32) ptx::tmem_st32_zero(trow + (uint32_t)col);
+        const int qtr = warp & 3;
+        const uint32_t trow = tmem + ((uint32_t)(32 * qtr) << 16);
+        for (int col = 0; col < NB * NSTREAM; col += 32) ptx::tmem_st32_zero(trow + (uint32_t)col);
         ptx::tmem_wait_st();
         ptx::tc_fence_before();
         __syncwarp();
         if (lane == 0)
-            for (int a = 0; a < NACC; ++a) ptx::mbar_arrive(bar(L::aempty(a)));
+            for (int p = 0; p < NSTREAM; ++p) ptx::mbar_arrive(bar(L::aempty(p)));
         bool ok = true;
-        uint32_t seg = 0;
+        uint32_t seg[NSTREAM] = {0, 0};
+        bool done[NSTREAM] = {false, false};
         const bool vec = (pl.gt & 3) == 0;
         // A and B carry neither c_s nor c_t: both join the normalisation here
         const float scale = pl.norm * (pl.cs * pl.ct);
-        while (ok) {
-            const int b = (int)(seg & 1u);
-            const uint32_t par = (seg >> 1) & 1u;
-            // the item of this segment is in its descriptor; stop after the CTA's last item
-            if (!(ok = wait_warp(c, bar(L::dfull(b)), par))) break;
-            if (!(ok = wait_warp(c, bar(L::afull(b)), par))) break;
+        while (ok && !(done[0] && done[1])) {
+            // the next segment of whichever stream has one ready (lane 0 picks)
+            int p = -1;
+            if (lane == 0) {
+                const uint64_t t0 = ptx::globaltimer();
+                for (uint32_t it = 0; p < 0; ++it) {
+                    for (int s = 0; s < NSTREAM && p < 0; ++s)
+                        if (!done[s] && ptx::mbar_try_wait_ns(bar(L::dfull(s)), seg[s] & 1u, 400)) p = s;
+                    if (p < 0 && (it & 7) == 7 && (*c.abort || timed_out(c, t0))) break;
+                }
+            }
+            p = __shfl_sync(0xffffffffu, p, 0);
+            if (p < 0) break;
+            if (!(ok = wait_warp(c, bar(L::dfull(p)), seg[p] & 1u))) break;
+            if (!(ok = wait_warp(c, bar(L::afull(p)), seg[p] & 1u))) break;
             ptx::tc_fence_after();
-            const int4 dsc = ptx::lds_i4(sb + L::OFF_DESC + b * 16);
+            const int4 dsc = ptx::lds_i4(sb + L::OFF_DESC + p * 16);
+            ++seg[p];
+            if (dsc.z & D_TERM) {
+                done[p] = true;
+                continue;
+            }
             const int64_t item = (int64_t)(uint32_t)dsc.x | ((int64_t)dsc.y << 32);
-            const bool first = (dsc.z & 1) != 0, last = (dsc.z & 2) != 0;
+            const bool first = (dsc.z & D_FIRST) != 0, last = (dsc.z & D_LAST) != 0;
             const uint32_t touched = (uint32_t)dsc.w;
             int tx, ty, tb;
             decode_item(pl, item, tx, ty, tb);
-            const int m = 32 * q + lane;
+            const int m = 32 * qtr + lane;
             const int X = tx * TX + m / TY, Y = ty * TY + m % TY, T0 = tb * NB;
             const int nbv = min(NB, pl.gt - T0);
             const bool valid = X < pl.gx && Y < pl.gy;
@@ -781,7 +810,7 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                 const bool hit = (touched >> (col >> 5)) & 1u;
                 if (!first && !hit) continue;
                 uint32_t r[32];
-                const uint32_t ta = trow + (uint32_t)(b * NB + col);
+                const uint32_t ta = trow + (uint32_t)(p * NB + col);
                 ptx::tmem_ld32(ta, r);
                 ptx::tmem_wait_ld();
                 if (hit) ptx::tmem_st32_zero(ta);
@@ -819,17 +848,15 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             ptx::tmem_wait_st();
             ptx::tc_fence_before();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(bar(L::aempty(b)));
-            ++seg;
-            if (last && item + gridDim.x >= nitems) break;
+            if (lane == 0) ptx::mbar_arrive(bar(L::aempty(p)));
         }
     }
 
     ptx::tc_fence_before();
     __syncthreads();
-    if (warp == WARP_MMA) {
+    if (warp == 0) {
         ptx::tc_fence_after();
-        ptx::tmem_dealloc(tmem, NB * NACC);
+        ptx::tmem_dealloc(tmem, NB * NSTREAM);
     }
 }
 
