@@ -213,6 +213,33 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- ours ---
 
+def recorded_traffic(args):
+    """DRAM bytes (read + write) of one tile-kernel launch from the committed ncu
+    summary, if it was taken on this workload and form with the current kernel
+    source; else None."""
+    if args.workload != "large" or args.form != "bf16x3":
+        return None
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "tile_tc_large_dram.md")
+    src = os.path.join(ROOT, "paper_1705_09366_gb300", "csrc", "tile_tc.cu")
+    if not (os.path.exists(prof) and os.path.exists(src)):
+        return None
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    rec = {}
+    with open(prof) as f:
+        for ln in f:
+            k, _, v = ln.strip().partition(":")
+            if k in ("tile_tc_sha256_prefix", "traffic_bytes_per_launch"):
+                rec[k] = v.strip()
+    if not rec.get("tile_tc_sha256_prefix") or not sha.startswith(rec["tile_tc_sha256_prefix"]):
+        return None
+    try:
+        return int(rec["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def run_ours(args):
     import torch
     import paper_1705_09366_gb300 as pkg
@@ -316,7 +343,7 @@ def run_ours(args):
     hbm = grid_bytes / (tile_ms * 1e-3) / 1e9
     roof["hbm_write_gbs"] = hbm
     roof["hbm_frac_of_" + peaks_src] = hbm / peaks["hbm_gbs"]
-    roof["traffic"] = None
+    roof["traffic"] = recorded_traffic(args)
     roof["kernel_ms"] = tile_ms
     roof["roofline_ms"] = 1e3 * max(grid_bytes / (peaks["hbm_gbs"] * 1e9),
                                     (flops / (peak * 1e12)))
