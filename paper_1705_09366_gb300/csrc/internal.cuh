@@ -67,8 +67,15 @@ void launch_tile_fp32(const Plan& pl, const Bins& b, float* out, int* err, cudaS
 void launch_scatter(const Plan& pl, const float4* ev, float* out, cudaStream_t st);
 
 // -------------------------------------------------------------- tile_tc.cu
-// Returns false if the form is not available in this build.
-bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int fp16,
-                    cudaStream_t st);
+// Tiles of the tensor tile kernel, and the bytes of its tile-ordering scratch.
+int64_t tile_tc_items(const Plan& pl);
+size_t tile_order_bytes(const Plan& pl);
+// Returns false if the form is not available in this build (or the problem has
+// 2^31 tiles or more).  tile_ctr: one device int, the launch's tile queue (zeroed
+// here on the stream before the kernel).  order_ws: tile_order_bytes(pl) of device
+// scratch for the heaviest-first tile order (two extra launches), or NULL to take
+// the tiles in index order.
+bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* tile_ctr,
+                    uint32_t* order_ws, int fp16, cudaStream_t st);
 
 }  // namespace stkde

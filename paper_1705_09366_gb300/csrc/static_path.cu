@@ -7,7 +7,8 @@
 // must not take the implicit device-wide synchronisation of cudaMalloc/cudaFree.
 // For them this entry point takes device inputs and outputs from the caller and
 // keeps all of its own scratch -- re-centred events, sort keys and indices, radix
-// histograms, bin boundaries, the sorted events and the device error word -- in
+// histograms, bin boundaries, the sorted events, the device error word and the
+// tensor kernel's tile queue -- in
 // one file-scope __device__ array of fixed size (about 16 MB, held by every
 // device that loads the library until the process exits).  It calls no
 // cudaMalloc, cudaFree or other allocating routine.
@@ -121,6 +122,7 @@ extern "C" stkde_status stkde_compute_static(const double* points, int64_t n,
     uint32_t* hist = reinterpret_cast<uint32_t*>(base + kOffHist);
     uint32_t* start = reinterpret_cast<uint32_t*>(base + kOffStart);
     int* err = reinterpret_cast<int*>(base + kOffErr);
+    int* tile_ctr = reinterpret_cast<int*>(base + kOffErr + 128);
     const size_t grid_bytes = sizeof(float) * (size_t)grid->gx * (size_t)grid->gy * (size_t)grid->gt;
 
     cudaMemsetAsync(err, 0, sizeof(int), st);  // the previous call's error word
@@ -138,7 +140,8 @@ extern "C" stkde_status stkde_compute_static(const double* points, int64_t n,
             Bins b{ev_sorted, start};
             if (form == STKDE_FORM_FP32) {
                 launch_tile_fp32(pl, b, out, err, st);
-            } else if (!launch_tile_tc(pl, b, out, err, form == STKDE_FORM_TENSOR_FP16X3 ? 1 : 0, st)) {
+            } else if (!launch_tile_tc(pl, b, out, err, tile_ctr, nullptr,
+                                       form == STKDE_FORM_TENSOR_FP16X3 ? 1 : 0, st)) {
                 return STKDE_ERR_UNSUPPORTED;
             }
         }

@@ -32,6 +32,7 @@ struct stkde_ctx {
     float* out_tmp = nullptr;  // device result buffer for host outputs
     size_t out_tmp_bytes = 0;
     int* d_err = nullptr;
+    int* d_ctr = nullptr;  // tile queue of the tensor tile kernel
     unsigned long long* d_count = nullptr;
     cudaEvent_t ev[MAX_PHASES + 1];
     int nphase = 0;
@@ -46,10 +47,12 @@ struct Workspace {
     float4* ev;
     float4* ev_sorted;
     uint32_t *keys, *idx, *keys_tmp, *idx_tmp, *hist, *start;
+    uint32_t* order;  // tile-ordering scratch of the tensor tile kernel
 };
 
-// Carves the workspace for n events and nkeys bins; returns the bytes needed.
-size_t carve(void* base, int n, uint32_t nkeys, bool host_points, Workspace* w) {
+// Carves the workspace for n events, nkeys bins and order_bytes of tile-ordering
+// scratch; returns the bytes needed.
+size_t carve(void* base, int n, uint32_t nkeys, bool host_points, size_t order_bytes, Workspace* w) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
         char* p = base ? static_cast<char*>(base) + off : nullptr;
@@ -67,6 +70,7 @@ size_t carve(void* base, int n, uint32_t nkeys, bool host_points, Workspace* w) 
     t.idx_tmp = reinterpret_cast<uint32_t*>(take(4 * nn));
     t.hist = reinterpret_cast<uint32_t*>(take(radix_sort_temp_bytes(n)));
     t.start = reinterpret_cast<uint32_t*>(take(4 * ((size_t)nkeys + 1)));
+    t.order = reinterpret_cast<uint32_t*>(take(order_bytes));
     if (w) *w = t;
     return off;
 }
@@ -191,8 +195,11 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
     if (form == STKDE_FORM_FP32) {
         launch_tile_fp32(pl, b, out, c->d_err, st);
     } else {
-        if (!launch_tile_tc(pl, b, out, c->d_err, form == STKDE_FORM_TENSOR_FP16X3 ? 1 : 0, st))
+        // heaviest tiles first (two small launches), then the tile kernel
+        if (!launch_tile_tc(pl, b, out, c->d_err, c->d_ctr, w.order,
+                            form == STKDE_FORM_TENSOR_FP16X3 ? 1 : 0, st))
             return STKDE_ERR_UNSUPPORTED;
+        c->launches += 2;
     }
     c->launches += 1;
     mark(c);
@@ -261,9 +268,11 @@ stkde_status stkde_create(stkde_ctx** out, const stkde_options* opt) {
     c->device = o.device;
     c->sm_count = prop.multiProcessorCount;
     if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_ctr, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         if (c->d_err) cudaFree(c->d_err);
+        if (c->d_ctr) cudaFree(c->d_ctr);
         delete c;
         return STKDE_ERR_OOM;
     }
@@ -283,6 +292,7 @@ void stkde_destroy(stkde_ctx* c) {
     if (c->ws) cudaFree(c->ws);
     if (c->out_tmp) cudaFree(c->out_tmp);
     if (c->d_err) cudaFree(c->d_err);
+    if (c->d_ctr) cudaFree(c->d_ctr);
     if (c->d_count) cudaFree(c->d_count);
     for (int i = 0; i <= MAX_PHASES; ++i)
         if (c->events_ok) cudaEventDestroy(c->ev[i]);
@@ -340,10 +350,12 @@ stkde_status stkde_compute(stkde_ctx* c, const double* points, int64_t n, const 
         if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
         const Plan pl = make_plan(c->opt.kernel_constants, n, g, hs, ht, c->opt.slab);
         Workspace w;
-        const size_t need = carve(nullptr, (int)n, pl.nkeys, pkind == 0, nullptr);
+        const bool tensor = c->opt.form == STKDE_FORM_TENSOR_BF16X3 || c->opt.form == STKDE_FORM_TENSOR_FP16X3;
+        const size_t order_bytes = tensor ? tile_order_bytes(pl) : 0;
+        const size_t need = carve(nullptr, (int)n, pl.nkeys, pkind == 0, order_bytes, nullptr);
         s = ensure_ws(c, need);
         if (s != STKDE_OK) return s;
-        carve(c->ws, (int)n, pl.nkeys, pkind == 0, &w);
+        carve(c->ws, (int)n, pl.nkeys, pkind == 0, order_bytes, &w);
         const double* dpts = points;
         if (pkind == 0) {
             cudaError_t e = cudaMemcpyAsync(w.pts, points, 24 * (size_t)n, cudaMemcpyHostToDevice,
@@ -378,9 +390,9 @@ stkde_status stkde_count_updates(stkde_ctx* c, const double* points, int64_t n,
     if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
     const Plan pl = make_plan(c->opt.kernel_constants, n, g, hs, ht, c->opt.slab);
     Workspace w;
-    s = ensure_ws(c, carve(nullptr, (int)n, pl.nkeys, pkind == 0, nullptr));
+    s = ensure_ws(c, carve(nullptr, (int)n, pl.nkeys, pkind == 0, 0, nullptr));
     if (s != STKDE_OK) return s;
-    carve(c->ws, (int)n, pl.nkeys, pkind == 0, &w);
+    carve(c->ws, (int)n, pl.nkeys, pkind == 0, 0, &w);
     const double* dpts = points;
     if (pkind == 0) {
         cudaMemcpyAsync(w.pts, points, 24 * (size_t)n, cudaMemcpyHostToDevice, c->stream);

@@ -22,10 +22,11 @@
 // with its own loader, four generators, stage ring, MMA warp and 256-column
 // accumulator; the four epilogue warps serve both.  One MMA warp issues at most
 // one entry every few hundred cycles (stage wait, header, three MMAs, commit),
-// so two streams double the issue rate.  Tiles are handed to the streams on
-// demand (a shared counter over the CTA's tiles); each tile is computed by one
-// stream in a fixed order, so the result does not depend on which stream or CTA
-// computes it.  Roles (warp w runs on scheduler w % 4):
+// so two streams double the issue rate.  Tiles are handed out on demand from one
+// global counter (zeroed before the launch) to whichever stream of whichever CTA
+// is free, which evens out the clustered workloads' uneven tiles; each tile is
+// computed by one stream in a fixed order, so the result does not depend on
+// which stream or CTA computes it.  Roles (warp w runs on scheduler w % 4):
 //   warps 0, 8        MMA issue for streams 0, 1 (the whole warp runs the loop,
 //                     one elected lane issues); warp 0 allocates tensor memory
 //   warps 4, 11       loaders: walk a tile's event bins and stage them, in bin
@@ -126,7 +127,7 @@ struct L {
     static constexpr uint32_t OFF_BAR = OFF_DESC + NSTREAM * 16;
     static constexpr int BARS_PER_STREAM = 3 * NPAGES + 2 * NSTAGE + 4;
     static constexpr int NBARS = NSTREAM * BARS_PER_STREAM;
-    static constexpr uint32_t OFF_MISC = OFF_BAR + NBARS * 8;  // tmem base, abort flag, tile counter
+    static constexpr uint32_t OFF_MISC = OFF_BAR + NBARS * 8;  // tmem base, abort flag
     static constexpr uint32_t TOTAL = OFF_MISC + 16;
     // barrier indices of stream p
     __host__ __device__ static constexpr int pfull(int p, int q) { return p * BARS_PER_STREAM + q; }
@@ -260,12 +261,12 @@ __device__ __forceinline__ void decode_item(const Plan& pl, int64_t item, int& t
 template <bool FP16>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ start,
-          float* __restrict__ out, int* __restrict__ err, int64_t nitems, int flush_chunks) {
+          float* __restrict__ out, int* __restrict__ err, int* __restrict__ tile_ctr,
+          const uint32_t* __restrict__ order, int64_t nitems, int flush_chunks) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const uint32_t sb = ptx::smem_addr(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Ctl c{reinterpret_cast<volatile int*>(smem + L::OFF_MISC + 4), err};
-    int* next_tile = reinterpret_cast<int*>(smem + L::OFF_MISC + 8);
     auto bar = [sb](int i) -> uint32_t { return sb + L::OFF_BAR + 8u * (uint32_t)i; };
     int4* pmeta = reinterpret_cast<int4*>(smem + L::OFF_PMETA);   // [stream][page][2]
     int4* pkept = reinterpret_cast<int4*>(smem + L::OFF_KEPT);    // [stream][page]
@@ -289,7 +290,6 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             ptx::mbar_init(bar(L::drain(p)), 1);
         }
         *c.abort = 0;
-        *next_tile = 0;
         ptx::fence_mbar_init();
     }
     if (warp == 0) {
@@ -422,12 +422,15 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             if (!(flags & P_TERM)) ok = ok && filter_upto(pg - 1);
         };
         while (ok) {
-            // the CTA's tiles are blockIdx.x + k * gridDim.x; take the next k
+            // the next tile of the launch's global queue (heaviest first when ordered)
             int k = 0;
-            if (lane == 0) k = atomicAdd(next_tile, 1);
-            k = __shfl_sync(0xffffffffu, k, 0);
-            const int64_t item = (int64_t)blockIdx.x + (int64_t)k * gridDim.x;
-            if (item >= nitems) break;
+            if (lane == 0) {
+                k = atomicAdd(tile_ctr, 1);
+                if (order && k < nitems) k = (int)order[k];
+            }
+            const int64_t kk = (int64_t)__shfl_sync(0xffffffffu, k, 0);
+            if (kk >= nitems) break;
+            const int64_t item = kk;
             int tx, ty, tb;
             decode_item(pl, item, tx, ty, tb);
             const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
@@ -860,8 +863,45 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
     }
 }
 
+// Tile ordering, heaviest first (an LPT schedule for the tile queue: the
+// clustered workloads' tiles differ in cost by orders of magnitude, and a heavy
+// tile started last sets the kernel's tail).  Cost of a tile = events in its bin
+// neighbourhood; tiles are bucketed by floor(log2(cost + 1)), buckets in
+// descending order; the order inside a bucket does not matter (each tile is
+// computed independently and deterministically).
+constexpr int NBUCKET = 33;
+
+__global__ void k_tile_cost(Plan pl, const uint32_t* __restrict__ start, int nitems,
+                            uint32_t* __restrict__ cost, uint32_t* __restrict__ hist) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nitems) return;
+    int tx, ty, tb;
+    decode_item(pl, i, tx, ty, tb);
+    const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
+    uint32_t sum = 0;
+    for (int s = g.s_lo; s <= g.s_hi; ++s)
+        for (int cx = g.cx_lo; cx <= g.cx_hi; ++cx) {
+            const uint32_t kb = ((uint32_t)s * (uint32_t)pl.ntx + (uint32_t)cx) * (uint32_t)pl.nty;
+            sum += start[kb + g.cy_hi + 1] - start[kb + g.cy_lo];
+        }
+    cost[i] = sum;
+    atomicAdd(&hist[32 - __clz(sum)], 1u);
+}
+
+__global__ void k_tile_order(int nitems, const uint32_t* __restrict__ cost,
+                             const uint32_t* __restrict__ hist, uint32_t* __restrict__ cursor,
+                             uint32_t* __restrict__ order) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nitems) return;
+    const int b = 32 - __clz(cost[i]);
+    uint32_t base = 0;
+    for (int h = NBUCKET - 1; h > b; --h) base += hist[h];
+    order[base + atomicAdd(&cursor[b], 1u)] = (uint32_t)i;
+}
+
 template <bool FP16>
-bool launch_cfg(const Plan& pl, const Bins& b, float* out, int* err, cudaStream_t st) {
+bool launch_cfg(const Plan& pl, const Bins& b, float* out, int* err, int* tile_ctr,
+                uint32_t* order_ws, cudaStream_t st) {
     auto kern = k_tile_tc<FP16>;
     static bool attr = false;
     if (!attr) {
@@ -876,20 +916,44 @@ bool launch_cfg(const Plan& pl, const Bins& b, float* out, int* err, cudaStream_
     const int ntb = (pl.gt + NB - 1) / NB;
     const int64_t items = (int64_t)pl.ntx * pl.nty * ntb;
     if (items <= 0) return true;
+    if (items >= (int64_t)1 << 31) return false;  // the tile queue counts in int
     const int grid = (int)(items < sms ? items : sms);
+    if (cudaMemsetAsync(tile_ctr, 0, sizeof(int), st) != cudaSuccess) return false;
+    const uint32_t* order = nullptr;
+    if (order_ws) {
+        uint32_t* hist = order_ws;
+        uint32_t* cursor = order_ws + 64;
+        uint32_t* cost = order_ws + 128;
+        uint32_t* ord = cost + items;
+        if (cudaMemsetAsync(order_ws, 0, 128 * sizeof(uint32_t), st) != cudaSuccess) return false;
+        const int blocks = (int)((items + 255) / 256);
+        k_tile_cost<<<blocks, 256, 0, st>>>(pl, b.start, (int)items, cost, hist);
+        k_tile_order<<<blocks, 256, 0, st>>>((int)items, cost, hist, cursor, ord);
+        order = ord;
+    }
     // chunks (three accumulation steps each) per 32-column block at which a
     // segment is closed (a power of two: the MMA warp tests it as a bit mask):
     // bounds the round-toward-zero drift of the tensor-core accumulation per segment
     const int flush_chunks = FP16 ? 64 : 128;
-    kern<<<grid, NTHREADS, L::TOTAL, st>>>(pl, b.ev, b.start, out, err, items, flush_chunks);
+    kern<<<grid, NTHREADS, L::TOTAL, st>>>(pl, b.ev, b.start, out, err, tile_ctr, order, items,
+                                           flush_chunks);
     return true;
 }
 
 }  // namespace
 
-bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int fp16,
-                    cudaStream_t st) {
-    return fp16 ? launch_cfg<true>(pl, b, out, err, st) : launch_cfg<false>(pl, b, out, err, st);
+int64_t tile_tc_items(const Plan& pl) {
+    return (int64_t)pl.ntx * pl.nty * ((pl.gt + NB - 1) / NB);
+}
+
+size_t tile_order_bytes(const Plan& pl) {
+    return sizeof(uint32_t) * (128 + 2 * (size_t)tile_tc_items(pl));
+}
+
+bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* tile_ctr,
+                    uint32_t* order_ws, int fp16, cudaStream_t st) {
+    return fp16 ? launch_cfg<true>(pl, b, out, err, tile_ctr, order_ws, st)
+                : launch_cfg<false>(pl, b, out, err, tile_ctr, order_ws, st);
 }
 
 }  // namespace stkde
