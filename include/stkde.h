@@ -129,10 +129,18 @@ typedef struct {
     float* out;            /* device memory, gx*gy*gt binary32 */
 } stkde_problem;
 
-/* Computes `count` independent problems with the tensor (or fp32) tile kernel
- * in one persistent launch whose work queue holds the tiles of all problems,
- * heaviest first.  Each result equals the problem computed alone with the same
- * form.  Outputs must be device memory. */
+/* Computes `count` independent problems in one batched call (the paper's
+ * runs are one problem each; batching is this library's addition for many small
+ * problems): one re-centre, one binning sort and one bin-bounds pass over the
+ * concatenated events of all problems, then, for the tensor forms, one
+ * persistent tile-kernel launch whose work queue holds the tiles of every
+ * problem, heaviest first (the fp32 form launches its tile kernel per problem).
+ * Each result is bit-identical to the problem computed alone by stkde_compute
+ * with the same form.  Events may be host or device memory per problem; outputs
+ * must be device memory of the context's device.  Errors: INVALID_ARGUMENT (any
+ * problem fails stkde_compute's checks, or an output is not device memory;
+ * nothing is enqueued), UNSUPPORTED (the scatter form, or a batch of 2^31 events,
+ * 2^32 bins or 2^31 tiles or more), OOM, CUDA.  count = 0 is a no-op. */
 STKDE_API stkde_status stkde_compute_batch(stkde_ctx* ctx, const stkde_problem* problems, int count);
 
 /* Number of (event, in-grid voxel) pairs inside the bandwidth cylinder

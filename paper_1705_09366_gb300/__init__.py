@@ -261,6 +261,19 @@ class Context:
         stkde_compute(self.handle, points, n, g, hs, ht, out)
         return out
 
+    def compute_batch(self, problems):
+        """Densities of several independent problems in one batched call.
+        ``problems``: iterable of (points, dims, hs, ht, out) with device ``out``
+        buffers (torch); returns the list of outputs."""
+        probs, keep = [], []
+        for pts, dims, hs, ht, out in problems:
+            gx, gy, gt = (int(d) for d in dims)
+            keep.append((pts, out))
+            probs.append(Problem(_ptr(pts) if int(pts.shape[0]) > 0 else None, int(pts.shape[0]),
+                                 make_grid(gx, gy, gt), float(hs), float(ht), _ptr(out)))
+        stkde_compute_batch(self.handle, probs)
+        return [o for _, o in keep]
+
     def synchronize(self):
         stkde_synchronize(self.handle)
 

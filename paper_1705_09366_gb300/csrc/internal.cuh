@@ -36,6 +36,23 @@ struct Plan {
     int n;                   // events
 };
 
+// One problem of a batched launch (a single problem is a batch of one): its
+// plan, its inputs and output, and its offsets in the batch's concatenated event,
+// bin-key and tile numberings.  Built on the host; the batch's table lives in
+// device memory.
+struct ProblemDev {
+    Plan pl;
+    const double* pts;        // n x 3 doubles, device memory
+    double x0, y0, t0, sres, tres, isres, itres;
+    int by_recip;             // both resolutions are powers of two: multiply by the exact reciprocal
+    uint32_t key_base;        // first bin key of the problem (its keys: key_base .. key_base + nkeys)
+    int64_t ev_base;          // first event of the problem in the batch's event numbering
+    int64_t item_base;        // first tile of the problem in the batch's tile numbering
+    const float4* ev;         // the batch's events sorted by key
+    const uint32_t* start;    // the problem's bin boundaries start[0 .. nkeys]
+    float* out;               // the problem's output grid, device memory
+};
+
 // Per-problem device buffers (views into the context's workspace).
 struct Bins {
     const float4* ev;        // re-centred events sorted by key: (x', y', t', bits(original index))
@@ -70,6 +87,7 @@ void launch_scatter(const Plan& pl, const float4* ev, float* out, cudaStream_t s
 // Tiles of the tensor tile kernel, and the bytes of its tile-ordering scratch.
 int64_t tile_tc_items(const Plan& pl);
 size_t tile_order_bytes(const Plan& pl);
+size_t tile_order_bytes_items(int64_t items);
 // Returns false if the form is not available in this build (or the problem has
 // 2^31 tiles or more).  tile_ctr: one device int, the launch's tile queue (zeroed
 // here on the stream before the kernel).  order_ws: tile_order_bytes(pl) of device
@@ -77,5 +95,15 @@ size_t tile_order_bytes(const Plan& pl);
 // the tiles in index order.
 bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* tile_ctr,
                     uint32_t* order_ws, int fp16, cudaStream_t st);
+// The same over the tiles of all problems of a batch in one launch: `table` is
+// the batch's problem table in device memory (nprob entries, item_base set to
+// the running sum of tile_tc_items), total_items the sum; order_ws holds
+// tile_order_bytes_items(total_items).
+bool launch_tile_tc_batch(const ProblemDev* table, int nprob, int64_t total_items, int* err,
+                          int* tile_ctr, uint32_t* order_ws, int fp16, cudaStream_t st);
+// K0 over all events of a batch: event i belongs to the problem whose ev_base
+// range holds it; keys are offset by the problem's key_base.
+void launch_recentre_batch(const ProblemDev* table, int nprob, int ntotal, float4* ev,
+                           uint32_t* keys, uint32_t* idx, int* err, cudaStream_t st);
 
 }  // namespace stkde

@@ -14,16 +14,17 @@ namespace stkde {
 
 // ------------------------------------------------------------------- K0 ---
 
-__global__ void k_recentre(const double* __restrict__ pts, int n, double x0, double y0,
-                           double t0, double sres, double tres, int by_recip, double isres,
-                           double itres, Plan pl, float4* __restrict__ ev,
-                           uint32_t* __restrict__ keys, uint32_t* __restrict__ idx,
-                           int* __restrict__ err) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double x = pts[3 * (size_t)i + 0];
-    const double y = pts[3 * (size_t)i + 1];
-    const double t = pts[3 * (size_t)i + 2];
+// Re-centres event i (row `row` of its problem's n x 3 array) and computes its
+// bin key, offset by the problem's first key.
+__device__ __forceinline__ void recentre_one(const double* __restrict__ row, double x0, double y0,
+                                             double t0, double sres, double tres, int by_recip,
+                                             double isres, double itres, const Plan& pl,
+                                             uint32_t key_base, int i, float4* __restrict__ ev,
+                                             uint32_t* __restrict__ keys, uint32_t* __restrict__ idx,
+                                             int* __restrict__ err) {
+    const double x = row[0];
+    const double y = row[1];
+    const double t = row[2];
     // Re-centre on the grid origin in FP64 (the only FP64 step of the path), then
     // round to binary32.  Division unless the resolution is a power of two, where
     // multiplying by the exact reciprocal gives the same bits.
@@ -54,8 +55,19 @@ __global__ void k_recentre(const double* __restrict__ pts, int n, double x0, dou
         key = ((uint32_t)s * (uint32_t)pl.ntx + (uint32_t)cx) * (uint32_t)pl.nty + (uint32_t)cy;
     }
     ev[i] = make_float4(fx, fy, ft, __int_as_float(i));
-    keys[i] = key;
+    keys[i] = key_base + key;
     idx[i] = (uint32_t)i;
+}
+
+__global__ void k_recentre(const double* __restrict__ pts, int n, double x0, double y0,
+                           double t0, double sres, double tres, int by_recip, double isres,
+                           double itres, Plan pl, float4* __restrict__ ev,
+                           uint32_t* __restrict__ keys, uint32_t* __restrict__ idx,
+                           int* __restrict__ err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    recentre_one(pts + 3 * (size_t)i, x0, y0, t0, sres, tres, by_recip, isres, itres, pl, 0u, i,
+                 ev, keys, idx, err);
 }
 
 void launch_recentre(const double* pts, int n, double x0, double y0, double t0, double sres,
@@ -66,6 +78,28 @@ void launch_recentre(const double* pts, int n, double x0, double y0, double t0, 
     const bool p2 = (frexp(sres, &e) == 0.5) && (frexp(tres, &e) == 0.5);
     k_recentre<<<(n + 255) / 256, 256, 0, st>>>(pts, n, x0, y0, t0, sres, tres, p2 ? 1 : 0,
                                                1.0 / sres, 1.0 / tres, pl, ev, keys, idx, err);
+}
+
+// The same over a batch: event i belongs to the last problem whose ev_base <= i.
+__global__ void k_recentre_batch(const ProblemDev* __restrict__ table, int nprob, int ntotal,
+                                 float4* __restrict__ ev, uint32_t* __restrict__ keys,
+                                 uint32_t* __restrict__ idx, int* __restrict__ err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntotal) return;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (table[mid].ev_base <= i) lo = mid; else hi = mid - 1;
+    }
+    const ProblemDev& P = table[lo];
+    recentre_one(P.pts + 3 * (size_t)(i - P.ev_base), P.x0, P.y0, P.t0, P.sres, P.tres, P.by_recip,
+                 P.isres, P.itres, P.pl, P.key_base, i, ev, keys, idx, err);
+}
+
+void launch_recentre_batch(const ProblemDev* table, int nprob, int ntotal, float4* ev,
+                           uint32_t* keys, uint32_t* idx, int* err, cudaStream_t st) {
+    if (ntotal <= 0 || nprob <= 0) return;
+    k_recentre_batch<<<(ntotal + 255) / 256, 256, 0, st>>>(table, nprob, ntotal, ev, keys, idx, err);
 }
 
 // ---------------------------------------------------------- radix sort ---

@@ -373,9 +373,146 @@ stkde_status stkde_compute(stkde_ctx* c, const double* points, int64_t n, const 
     return cuda_status(cudaGetLastError());
 }
 
+// Batched compute: one re-centre, one binning sort and one bounds + gather pass
+// over the concatenated events of all problems (keys offset per problem, so the
+// sort groups events by problem, then by bin), then one tile-kernel launch whose
+// heaviest-first queue holds the tiles of every problem (tensor forms), or one
+// fp32 tile launch per problem.  Each problem's result equals its own
+// stkde_compute with the same form: the same kernels see the same events in the
+// same order.
 stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int count) {
     if (!c || (count > 0 && !probs) || count < 0) return STKDE_ERR_INVALID_ARGUMENT;
-    return STKDE_ERR_UNSUPPORTED;
+    if (count == 0) return STKDE_OK;
+    const int form = c->opt.form;
+    if (form == STKDE_FORM_SCATTER) return STKDE_ERR_UNSUPPORTED;
+    const bool tensor = form == STKDE_FORM_TENSOR_BF16X3 || form == STKDE_FORM_TENSOR_FP16X3;
+    if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
+
+    // validate everything and lay the batch out before any launch
+    ProblemDev* tab = new (std::nothrow) ProblemDev[count];
+    int* pkinds = new (std::nothrow) int[count];
+    if (!tab || !pkinds) {
+        delete[] tab;
+        delete[] pkinds;
+        return STKDE_ERR_OOM;
+    }
+    struct Guard {
+        ProblemDev* t; int* k;
+        ~Guard() { delete[] t; delete[] k; }
+    } guard{tab, pkinds};
+    int64_t ntot = 0, itot = 0, host_events = 0;
+    uint64_t ktot = 0;
+    for (int i = 0; i < count; ++i) {
+        const stkde_problem& q = probs[i];
+        stkde_status s = check_problem(q.points, q.n, &q.grid, q.hs, q.ht);
+        if (s != STKDE_OK) return s;
+        if (!q.out || pointer_kind(q.out, c->device) != 1) return STKDE_ERR_INVALID_ARGUMENT;
+        pkinds[i] = q.n > 0 ? pointer_kind(q.points, c->device) : 1;
+        if (pkinds[i] < 0) return STKDE_ERR_INVALID_ARGUMENT;
+        ProblemDev& P = tab[i];
+        P = ProblemDev{};
+        P.pl = make_plan(c->opt.kernel_constants, q.n, &q.grid, q.hs, q.ht, c->opt.slab);
+        P.x0 = q.grid.x0; P.y0 = q.grid.y0; P.t0 = q.grid.t0;
+        P.sres = q.grid.sres; P.tres = q.grid.tres;
+        P.isres = 1.0 / q.grid.sres; P.itres = 1.0 / q.grid.tres;
+        int e2;
+        P.by_recip = (frexp(q.grid.sres, &e2) == 0.5) && (frexp(q.grid.tres, &e2) == 0.5);
+        P.key_base = (uint32_t)ktot;
+        P.ev_base = ntot;
+        P.item_base = itot;
+        ktot += (uint64_t)P.pl.nkeys + 1;  // the problem's bins and its "reaches nothing" key
+        ntot += q.n;
+        if (pkinds[i] == 0) host_events += q.n;
+        if (tensor) itot += tile_tc_items(P.pl);
+        if (ntot >= ((int64_t)1 << 31) || ktot >= ((uint64_t)1 << 32) || itot >= ((int64_t)1 << 31))
+            return STKDE_ERR_UNSUPPORTED;
+    }
+
+    // workspace: staging for host events, events, keys, sort scratch, bin bounds,
+    // tile-order scratch, the problem table
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes, 256);
+        return at;
+    };
+    const size_t nn = (size_t)(ntot > 0 ? ntot : 1);
+    const size_t o_pts = take(24 * (size_t)host_events);
+    const size_t o_ev = take(16 * nn), o_evs = take(16 * nn);
+    const size_t o_keys = take(4 * nn), o_idx = take(4 * nn), o_kt = take(4 * nn), o_it = take(4 * nn);
+    const size_t o_hist = take(radix_sort_temp_bytes((int)ntot));
+    const size_t o_start = take(4 * (size_t)ktot);
+    const size_t o_order = take(tensor ? tile_order_bytes_items(itot) : 0);
+    const size_t o_tab = take(sizeof(ProblemDev) * (size_t)count);
+    stkde_status s = ensure_ws(c, off);
+    if (s != STKDE_OK) return s;
+    char* base = static_cast<char*>(c->ws);
+    double* staging = reinterpret_cast<double*>(base + o_pts);
+    float4* ev = reinterpret_cast<float4*>(base + o_ev);
+    float4* ev_sorted = reinterpret_cast<float4*>(base + o_evs);
+    uint32_t* keys = reinterpret_cast<uint32_t*>(base + o_keys);
+    uint32_t* idx = reinterpret_cast<uint32_t*>(base + o_idx);
+    uint32_t* keys_tmp = reinterpret_cast<uint32_t*>(base + o_kt);
+    uint32_t* idx_tmp = reinterpret_cast<uint32_t*>(base + o_it);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(base + o_hist);
+    uint32_t* start = reinterpret_cast<uint32_t*>(base + o_start);
+    uint32_t* order = tensor ? reinterpret_cast<uint32_t*>(base + o_order) : nullptr;
+    ProblemDev* dtab = reinterpret_cast<ProblemDev*>(base + o_tab);
+
+    cudaStream_t st = c->stream;
+    c->nphase = 0;
+    c->launches = 0;
+    int64_t staged = 0;
+    for (int i = 0; i < count; ++i) {
+        ProblemDev& P = tab[i];
+        P.pts = probs[i].points;
+        if (pkinds[i] == 0 && probs[i].n > 0) {  // host events: copy into the staging area
+            double* dst = staging + 3 * staged;
+            const cudaError_t e = cudaMemcpyAsync(dst, probs[i].points, 24 * (size_t)probs[i].n,
+                                                  cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_status(e);
+            P.pts = dst;
+            staged += probs[i].n;
+        }
+        P.ev = ev_sorted;
+        P.start = start + P.key_base;
+        P.out = probs[i].out;
+    }
+    // the table is staged by the driver before cudaMemcpyAsync returns (pageable source)
+    cudaError_t e = cudaMemcpyAsync(dtab, tab, sizeof(ProblemDev) * (size_t)count,
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    int key_bits = 1;
+    while (key_bits < 32 && ((uint64_t)1 << key_bits) <= ktot - 1) ++key_bits;
+
+    mark(c);
+    launch_recentre_batch(dtab, count, (int)ntot, ev, keys, idx, c->d_err, st);
+    c->launches += ntot > 0 ? 1 : 0;
+    mark(c);
+    launch_radix_sort(keys, idx, keys_tmp, idx_tmp, hist, (int)ntot, key_bits, st);
+    c->launches += ntot > 1 ? 3 * ((key_bits + 7) / 8) : 0;
+    mark(c);
+    launch_bounds_gather(keys, idx, ev, (int)ntot, (uint32_t)(ktot - 1), start, ev_sorted, st);
+    c->launches += ntot > 0 ? 2 : 1;
+    mark(c);
+    if (tensor) {
+        if (!launch_tile_tc_batch(dtab, count, itot, c->d_err, c->d_ctr, order,
+                                  form == STKDE_FORM_TENSOR_FP16X3 ? 1 : 0, st))
+            return STKDE_ERR_UNSUPPORTED;
+        c->launches += itot > 0 ? 3 : 0;
+    } else {
+        for (int i = 0; i < count; ++i) {
+            const Plan& pl = tab[i].pl;
+            if (probs[i].n == 0) {
+                cudaMemsetAsync(probs[i].out, 0, sizeof(float) * (size_t)pl.gx * pl.gy * pl.gt, st);
+                continue;
+            }
+            launch_tile_fp32(pl, Bins{ev_sorted, start + tab[i].key_base}, probs[i].out, c->d_err, st);
+            c->launches += 1;
+        }
+    }
+    mark(c);
+    return cuda_status(cudaGetLastError());
 }
 
 stkde_status stkde_count_updates(stkde_ctx* c, const double* points, int64_t n,

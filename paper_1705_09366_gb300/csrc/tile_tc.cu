@@ -120,7 +120,7 @@ struct L {
     static constexpr uint32_t OFF_TAB = OFF_PAGES + NSTREAM * NPAGES * PAGE * 16;
     static constexpr uint32_t OFF_HDR = OFF_TAB + NSTREAM * NGEN * TAB_BYTES;
     static constexpr uint32_t OFF_PMETA = OFF_HDR + NSTREAM * NSTAGE * 32;
-    static constexpr uint32_t OFF_KEPT = OFF_PMETA + NSTREAM * NPAGES * 32;
+    static constexpr uint32_t OFF_KEPT = OFF_PMETA + NSTREAM * NPAGES * 48;
     static constexpr uint32_t OFF_CTAB = OFF_KEPT + NSTREAM * NPAGES * 16;
     static constexpr uint32_t OFF_ENT = OFF_CTAB + NSTREAM * NPAGES * MAXCH * 8;
     static constexpr uint32_t OFF_DESC = OFF_ENT + NSTREAM * NPAGES * MAXENT * 2;
@@ -258,17 +258,34 @@ __device__ __forceinline__ void decode_item(const Plan& pl, int64_t item, int& t
     tb = (int)(item / ((int64_t)pl.nty * pl.ntx));
 }
 
+// Problem of batch tile g: the last problem whose first tile is <= g.
+__device__ __forceinline__ int problem_of(const ProblemDev* __restrict__ table, int nprob, int64_t g) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (table[mid].item_base <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Problem p of the launch: the batch table's entry, or the single problem passed
+// by value.
+__device__ __forceinline__ ProblemDev fetch_problem(const ProblemDev& single,
+                                                    const ProblemDev* __restrict__ table, int p) {
+    return table ? table[p] : single;
+}
+
 template <bool FP16>
 __global__ void __launch_bounds__(NTHREADS, 1)
-k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ start,
-          float* __restrict__ out, int* __restrict__ err, int* __restrict__ tile_ctr,
-          const uint32_t* __restrict__ order, int64_t nitems, int flush_chunks) {
+k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
+          int* __restrict__ err, int* __restrict__ tile_ctr, const uint32_t* __restrict__ order,
+          int64_t nitems, int flush_chunks) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const uint32_t sb = ptx::smem_addr(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Ctl c{reinterpret_cast<volatile int*>(smem + L::OFF_MISC + 4), err};
     auto bar = [sb](int i) -> uint32_t { return sb + L::OFF_BAR + 8u * (uint32_t)i; };
-    int4* pmeta = reinterpret_cast<int4*>(smem + L::OFF_PMETA);   // [stream][page][2]
+    int4* pmeta = reinterpret_cast<int4*>(smem + L::OFF_PMETA);   // [stream][page][3]
     int4* pkept = reinterpret_cast<int4*>(smem + L::OFF_KEPT);    // [stream][page]
     int2* ctab = reinterpret_cast<int2*>(smem + L::OFF_CTAB);     // [stream][page][chunk]
     uint16_t* pent = reinterpret_cast<uint16_t*>(smem + L::OFF_ENT);  // [stream][page][entry]
@@ -323,9 +340,10 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             float4* fb = reinterpret_cast<float4*>(smem + L::OFF_PAGES + fp * PAGE * 16);
             int2* ct = ctab + fp * MAXCH;
             uint16_t* ent = pent + fp * MAXENT;
-            const int4 fm = pmeta[2 * fp], fmt4 = pmeta[2 * fp + 1];
+            const int4 fm = pmeta[3 * fp], fmt4 = pmeta[3 * fp + 1];
             uint32_t kept = 0, nent = 0;
             if (!(fm.y & P_TERM)) {
+                const Plan pl = fetch_problem(single, table, fmt4.w).pl;
                 const TileGeom fg = tile_geom(pl, fmt4.x, fmt4.y, fmt4.z, NB);
                 for (int r = 0; r * 32 < fm.x; ++r) {
                     const int slot = r * 32 + lane;
@@ -408,12 +426,13 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             }
             return true;
         };
-        auto close_page = [&](int flags, int64_t item, int tx, int ty, int tb) {
+        auto close_page = [&](int flags, int64_t item, int tx, int ty, int tb, int pi, float ihs, float iht) {
             __syncwarp();
             if (lane == 0) {
                 const uint32_t q = p * NPAGES + pg % NPAGES;
-                pmeta[2 * q] = make_int4((int)fill, flags, (int)(item & 0xffffffff), (int)(item >> 32));
-                pmeta[2 * q + 1] = make_int4(tx, ty, tb, 0);
+                pmeta[3 * q] = make_int4((int)fill, flags, (int)(item & 0xffffffff), (int)(item >> 32));
+                pmeta[3 * q + 1] = make_int4(tx, ty, tb, pi);
+                pmeta[3 * q + 2] = make_int4(__float_as_int(ihs), __float_as_int(iht), 0, 0);
                 ptx::mbar_arrive(bar(L::pfull(p, pg % NPAGES)));
             }
             __syncwarp();
@@ -428,9 +447,14 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                 k = atomicAdd(tile_ctr, 1);
                 if (order && k < nitems) k = (int)order[k];
             }
-            const int64_t kk = (int64_t)__shfl_sync(0xffffffffu, k, 0);
-            if (kk >= nitems) break;
-            const int64_t item = kk;
+            const int64_t gk = (int64_t)__shfl_sync(0xffffffffu, k, 0);
+            if (gk >= nitems) break;
+            const int pi = table ? problem_of(table, nprob, gk) : 0;
+            const ProblemDev P = fetch_problem(single, table, pi);
+            const Plan& pl = P.pl;
+            const float4* __restrict__ ev = P.ev;
+            const uint32_t* __restrict__ start = P.start;
+            const int64_t item = gk - P.item_base;  // tile of the problem
             int tx, ty, tb;
             decode_item(pl, item, tx, ty, tb);
             const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
@@ -469,18 +493,18 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                     }
                     fill += take;
                     done += take;
-                    if (fill == (uint32_t)PAGE) close_page(0, item, tx, ty, tb);
+                    if (fill == (uint32_t)PAGE) close_page(0, item, tx, ty, tb, pi, pl.inv_hs, pl.inv_ht);
                 }
             }
             if (!ok) break;
             if (!open && !(ok = open_page())) break;
-            close_page(P_ITEM_END, item, tx, ty, tb);  // the tile's last page, possibly empty
+            close_page(P_ITEM_END, item, tx, ty, tb, pi, pl.inv_hs, pl.inv_ht);  // the tile's last page, possibly empty
         }
         // termination page (every generator of the stream reads every page)
         if (ok) ok = filter_upto(pg);
-        if (ok && (ok = open_page())) close_page(P_TERM, 0, 0, 0, 0);
+        if (ok && (ok = open_page())) close_page(P_TERM, 0, 0, 0, 0, 0, 0.f, 0.f);
         if (!ok) {
-            if (open) close_page(P_TERM, 0, 0, 0, 0);
+            if (open) close_page(P_TERM, 0, 0, 0, 0, 0, 0.f, 0.f);
             for (uint32_t q = (pg > NPAGES ? pg - NPAGES : 0); q < pg; ++q)
                 drain_bar(bar(L::pfull(p, q % NPAGES)), (q / NPAGES) & 1u);
         }
@@ -491,7 +515,6 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
         float* xa = reinterpret_cast<float*>(tab + TAB_XA);
         float* yb = reinterpret_cast<float*>(tab + TAB_YB);
         float* tkt = reinterpret_cast<float*>(tab + TAB_TK);
-        const float inv_hs = pl.inv_hs, inv_ht = pl.inv_ht;
         const uint32_t fmt = FP16 ? 0u : 1u;
         bool ok = true;
         uint32_t ebase = 0;  // the stream's entries before the current page
@@ -506,7 +529,7 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
         // hands entry e to the stream's MMA warp, with what it needs precomputed:
         // the instruction descriptor, the 32-column blocks the MMAs touch and the
         // per-block chunk-count increments (bytes, four blocks per word)
-        auto publish = [&](uint32_t e, int c0, int ncols, int flags, int64_t item) {
+        auto publish = [&](uint32_t e, int c0, int ncols, int flags, int64_t item, int pi) {
             const uint32_t s = e % NSTAGE;
             if (lane == 0) {
                 uint32_t idesc = 0, mask = 0, inc_lo = 0, inc_hi = 0;
@@ -519,7 +542,7 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                 }
                 int4* h = reinterpret_cast<int4*>(smem + L::OFF_HDR + (p * NSTAGE + s) * 32);
                 h[0] = make_int4(c0, (int)idesc, flags, (int)mask);
-                h[1] = make_int4((int)inc_lo, (int)inc_hi, (int)(item & 0xffffffff), (int)(item >> 32));
+                h[1] = make_int4((int)inc_lo, (int)inc_hi, (int)item, pi);
             }
             ptx::fence_proxy_async_smem();
             __syncwarp();
@@ -530,13 +553,15 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             const uint32_t ph = (q / NPAGES) & 1u;
             const float4* page = reinterpret_cast<const float4*>(smem + L::OFF_PAGES + pq * PAGE * 16);
             if (!(ok = wait_warp(c, bar(L::pfull(p, q % NPAGES)), ph))) break;
-            const int4 meta = pmeta[2 * pq], mt = pmeta[2 * pq + 1];
+            const int4 meta = pmeta[3 * pq], mt = pmeta[3 * pq + 1], mr = pmeta[3 * pq + 2];
             if (meta.y & P_TERM) {
                 // the stream's sequence ends with entry ebase
-                if (ebase % NGEN == (uint32_t)gi && (ok = slot_wait(ebase))) publish(ebase, 0, 0, F_TERM, 0);
+                if (ebase % NGEN == (uint32_t)gi && (ok = slot_wait(ebase))) publish(ebase, 0, 0, F_TERM, 0, 0);
                 break;
             }
             const int64_t item = (int64_t)(uint32_t)meta.z | ((int64_t)meta.w << 32);
+            const int pi = mt.w;
+            const float inv_hs = __int_as_float(mr.x), inv_ht = __int_as_float(mr.y);
             const int end = meta.y & P_ITEM_END;
             const int X0 = mt.x * TX, Y0 = mt.y * TY, T0 = mt.z * NB;
             if (!(ok = wait_warp(c, bar(L::pfilt(p, q % NPAGES)), ph))) break;
@@ -555,7 +580,7 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                 if (code == 0xffffu) {
                     // end marker of a tile whose last page keeps nothing
                     if (!(ok = slot_wait(e))) break;
-                    publish(e, 0, 0, F_ITEM_END, item);
+                    publish(e, 0, 0, F_ITEM_END, item, pi);
                     continue;
                 }
                 const int ch = (int)(code & 0xffu), w = (int)(code >> 8);
@@ -666,7 +691,7 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                     }
                 }
                 const int fl = F_MMA | ((end && ch == nch - 1 && w + 1 == nw) ? F_ITEM_END : 0);
-                publish(e, cw, ncols, fl, item);
+                publish(e, cw, ncols, fl, item, pi);
             }
             if (!ok) break;
             // done with the page (only read here; the owner fenced its compaction)
@@ -697,9 +722,9 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
         uint32_t cnt_lo = 0, cnt_hi = 0;  // chunks per 32-column block (bytes)
         // hands the current segment to the epilogue and waits until it has been
         // drained (this stream has one accumulator)
-        auto close_segment = [&](int64_t item, int flags) -> bool {
+        auto close_segment = [&](int tile, int pi, int flags) -> bool {
             if (lane == 0) {
-                *desc = make_int4((int)(item & 0xffffffff), (int)(item >> 32), flags, (int)touched);
+                *desc = make_int4(tile, pi, flags, (int)touched);
                 ptx::mbar_arrive(bar(L::dfull(p)));
             }
             __syncwarp();
@@ -722,10 +747,10 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
             const int4 h0 = hdr[2 * s], h1 = hdr[2 * s + 1];
             const int flags = h0.z;
             if (flags & F_TERM) {
-                close_segment(0, D_TERM);
+                close_segment(0, 0, D_TERM);
                 break;
             }
-            const int64_t item = (int64_t)(uint32_t)h1.z | ((int64_t)h1.w << 32);
+            const int tile = h1.z, pi = h1.w;
             if (flags & F_MMA) {
                 const int c0 = h0.x;
                 const uint32_t idesc = (uint32_t)h0.y;
@@ -741,7 +766,7 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                     // power-of-two flush count closes the segment first
                     if (((cnt_lo + inc_lo) | (cnt_hi + inc_hi)) & flush4) {
                         // close the segment: the epilogue adds it in fp32
-                        if (!(ok = close_segment(item, first ? D_FIRST : 0))) break;
+                        if (!(ok = close_segment(tile, pi, first ? D_FIRST : 0))) break;
                         first = 0;
                     }
                     cnt_lo += inc_lo;
@@ -752,7 +777,7 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                 }
             }
             if (flags & F_ITEM_END) {
-                if (!(ok = close_segment(item, (first ? D_FIRST : 0) | D_LAST))) break;
+                if (!(ok = close_segment(tile, pi, (first ? D_FIRST : 0) | D_LAST))) break;
                 first = 1;
             }
             commit_elect(bar(L::sempty(p, s)));
@@ -774,9 +799,6 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
         bool ok = true;
         uint32_t seg[NSTREAM] = {0, 0};
         bool done[NSTREAM] = {false, false};
-        const bool vec = (pl.gt & 3) == 0;
-        // A and B carry neither c_s nor c_t: both join the normalisation here
-        const float scale = pl.norm * (pl.cs * pl.ct);
         while (ok && !(done[0] && done[1])) {
             // the next segment of whichever stream has one ready (lane 0 picks)
             int p = -1;
@@ -799,7 +821,13 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
                 done[p] = true;
                 continue;
             }
-            const int64_t item = (int64_t)(uint32_t)dsc.x | ((int64_t)dsc.y << 32);
+            const int64_t item = dsc.x;
+            const ProblemDev P = fetch_problem(single, table, dsc.y);
+            const Plan& pl = P.pl;
+            float* __restrict__ out = P.out;
+            const bool vec = (pl.gt & 3) == 0;
+            // A and B carry neither c_s nor c_t: both join the normalisation here
+            const float scale = pl.norm * (pl.cs * pl.ct);
             const bool first = (dsc.z & D_FIRST) != 0, last = (dsc.z & D_LAST) != 0;
             const uint32_t touched = (uint32_t)dsc.w;
             int tx, ty, tb;
@@ -871,12 +899,15 @@ k_tile_tc(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ s
 // computed independently and deterministically).
 constexpr int NBUCKET = 33;
 
-__global__ void k_tile_cost(Plan pl, const uint32_t* __restrict__ start, int nitems,
-                            uint32_t* __restrict__ cost, uint32_t* __restrict__ hist) {
+__global__ void k_tile_cost(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
+                            int nitems, uint32_t* __restrict__ cost, uint32_t* __restrict__ hist) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nitems) return;
+    const ProblemDev P = fetch_problem(single, table, table ? problem_of(table, nprob, i) : 0);
+    const Plan& pl = P.pl;
+    const uint32_t* __restrict__ start = P.start;
     int tx, ty, tb;
-    decode_item(pl, i, tx, ty, tb);
+    decode_item(pl, i - P.item_base, tx, ty, tb);
     const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
     uint32_t sum = 0;
     for (int s = g.s_lo; s <= g.s_hi; ++s)
@@ -900,8 +931,8 @@ __global__ void k_tile_order(int nitems, const uint32_t* __restrict__ cost,
 }
 
 template <bool FP16>
-bool launch_cfg(const Plan& pl, const Bins& b, float* out, int* err, int* tile_ctr,
-                uint32_t* order_ws, cudaStream_t st) {
+bool launch_cfg(const ProblemDev& single, const ProblemDev* table, int nprob, int64_t items,
+                int* err, int* tile_ctr, uint32_t* order_ws, cudaStream_t st) {
     auto kern = k_tile_tc<FP16>;
     static bool attr = false;
     if (!attr) {
@@ -913,8 +944,6 @@ bool launch_cfg(const Plan& pl, const Bins& b, float* out, int* err, int* tile_c
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int ntb = (pl.gt + NB - 1) / NB;
-    const int64_t items = (int64_t)pl.ntx * pl.nty * ntb;
     if (items <= 0) return true;
     if (items >= (int64_t)1 << 31) return false;  // the tile queue counts in int
     const int grid = (int)(items < sms ? items : sms);
@@ -927,7 +956,7 @@ bool launch_cfg(const Plan& pl, const Bins& b, float* out, int* err, int* tile_c
         uint32_t* ord = cost + items;
         if (cudaMemsetAsync(order_ws, 0, 128 * sizeof(uint32_t), st) != cudaSuccess) return false;
         const int blocks = (int)((items + 255) / 256);
-        k_tile_cost<<<blocks, 256, 0, st>>>(pl, b.start, (int)items, cost, hist);
+        k_tile_cost<<<blocks, 256, 0, st>>>(single, table, nprob, (int)items, cost, hist);
         k_tile_order<<<blocks, 256, 0, st>>>((int)items, cost, hist, cursor, ord);
         order = ord;
     }
@@ -935,7 +964,7 @@ bool launch_cfg(const Plan& pl, const Bins& b, float* out, int* err, int* tile_c
     // segment is closed (a power of two: the MMA warp tests it as a bit mask):
     // bounds the round-toward-zero drift of the tensor-core accumulation per segment
     const int flush_chunks = FP16 ? 64 : 128;
-    kern<<<grid, NTHREADS, L::TOTAL, st>>>(pl, b.ev, b.start, out, err, tile_ctr, order, items,
+    kern<<<grid, NTHREADS, L::TOTAL, st>>>(single, table, nprob, err, tile_ctr, order, items,
                                            flush_chunks);
     return true;
 }
@@ -946,14 +975,31 @@ int64_t tile_tc_items(const Plan& pl) {
     return (int64_t)pl.ntx * pl.nty * ((pl.gt + NB - 1) / NB);
 }
 
-size_t tile_order_bytes(const Plan& pl) {
-    return sizeof(uint32_t) * (128 + 2 * (size_t)tile_tc_items(pl));
+size_t tile_order_bytes_items(int64_t items) {
+    return sizeof(uint32_t) * (128 + 2 * (size_t)(items > 0 ? items : 0));
 }
+
+size_t tile_order_bytes(const Plan& pl) { return tile_order_bytes_items(tile_tc_items(pl)); }
 
 bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* tile_ctr,
                     uint32_t* order_ws, int fp16, cudaStream_t st) {
-    return fp16 ? launch_cfg<true>(pl, b, out, err, tile_ctr, order_ws, st)
-                : launch_cfg<false>(pl, b, out, err, tile_ctr, order_ws, st);
+    ProblemDev single{};
+    single.pl = pl;
+    single.ev = b.ev;
+    single.start = b.start;
+    single.out = out;
+    single.item_base = 0;
+    const int64_t items = tile_tc_items(pl);
+    return fp16 ? launch_cfg<true>(single, nullptr, 1, items, err, tile_ctr, order_ws, st)
+                : launch_cfg<false>(single, nullptr, 1, items, err, tile_ctr, order_ws, st);
+}
+
+bool launch_tile_tc_batch(const ProblemDev* table, int nprob, int64_t total_items, int* err,
+                          int* tile_ctr, uint32_t* order_ws, int fp16, cudaStream_t st) {
+    if (nprob <= 0) return true;
+    const ProblemDev none{};
+    return fp16 ? launch_cfg<true>(none, table, nprob, total_items, err, tile_ctr, order_ws, st)
+                : launch_cfg<false>(none, table, nprob, total_items, err, tile_ctr, order_ws, st);
 }
 
 }  // namespace stkde
