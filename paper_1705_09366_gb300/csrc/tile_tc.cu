@@ -330,10 +330,12 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             fill = 0;
             return true;
         };
-        // page meta: fill, flags, item, and the item's tile coordinates
         // Keeps the events of page fq (staged by this loader) whose cylinder
         // reaches their tile, compacted in place; records per chunk the covered
         // columns and the page's entry table; publishes the kept and entry counts.
+        // The whole page is read into registers first (8 rounds of 32 events), so
+        // the filter pays one shared-memory latency instead of one per round; the
+        // chunks' column ranges are folded in with shared-memory min/max atomics.
         const uint32_t lt = (1u << lane) - 1u;
         auto filter_page = [&](uint32_t fq) {
             const uint32_t fp = p * NPAGES + fq % NPAGES;
@@ -345,47 +347,41 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             if (!(fm.y & P_TERM)) {
                 const Plan pl = fetch_problem(single, table, fmt4.w).pl;
                 const TileGeom fg = tile_geom(pl, fmt4.x, fmt4.y, fmt4.z, NB);
-                for (int r = 0; r * 32 < fm.x; ++r) {
-                    const int slot = r * 32 + lane;
-                    float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-                    bool keep = false;
-                    if (slot < fm.x) {
-                        e = fb[slot];
-                        keep = reaches(pl, fg, e);
-                    }
-                    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-                    __syncwarp();
-                    if (keep) fb[kept + __popc(bal & lt)] = e;
-                    kept += __popc(bal);
-                    __syncwarp();
-                }
+                const int nev = fm.x, T0 = fg.T0, nbv = fg.T1 - fg.T0;
+                constexpr int R = PAGE / 32;
+                float4 e[R];
+                uint32_t bal[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) e[r] = fb[r * 32 + lane];
+                if (lane < MAXCH) ct[lane] = make_int2(0x7fffffff, -1);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    bal[r] = __ballot_sync(0xffffffffu, r * 32 + lane < nev && reaches(pl, fg, e[r]));
+                __syncwarp();  // every read of the page before the first compacting write
                 // columns covered by each chunk's windows, clipped into the block
                 // (the filter's margin can keep an event whose window misses the
                 // block; its K_t values are zero anyway)
-                const int nch = (int)(kept + CHUNK - 1) / CHUNK;
-                const int T0 = fg.T0, nbv = fg.T1 - fg.T0;
-                for (int r = 0; r * 32 < (int)kept; ++r) {
-                    const int slot = r * 32 + lane;
-                    int lo = 0x7fffffff, hi = -1;
-                    if (slot < (int)kept) {
-                        const float z = fb[slot].z;
-                        lo = min(max((int)ceilf(z - 0.5f - pl.htv) - T0, 0), nbv - 1);
-                        hi = min(max((int)floorf(z - 0.5f + pl.htv) - T0, lo), nbv - 1);
-                    }
 #pragma unroll
-                    for (int o = 8; o > 0; o >>= 1) {
-                        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                for (int r = 0; r < R; ++r) {
+                    if ((bal[r] >> lane) & 1u) {
+                        const uint32_t at = kept + __popc(bal[r] & lt);
+                        fb[at] = e[r];
+                        const float z = e[r].z;
+                        const int lo = min(max((int)ceilf(z - 0.5f - pl.htv) - T0, 0), nbv - 1);
+                        const int hi = min(max((int)floorf(z - 0.5f + pl.htv) - T0, lo), nbv - 1);
+                        atomicMin(&ct[at / CHUNK].x, lo);
+                        atomicMax(&ct[at / CHUNK].y, hi);
                     }
-                    const int ch = 2 * r + (lane >> 4);
-                    if ((lane & 15) == 0 && ch < nch)
-                        ct[ch] = make_int2((lo & ~15) | (((hi + 16) & ~15) << 16), 0);
+                    kept += __popc(bal[r]);
                 }
                 __syncwarp();
+                const int nch = (int)(kept + CHUNK - 1) / CHUNK;
                 // entries per chunk (column windows of up to NCAP) and their offsets
                 uint32_t nw = 0;
+                int2 t = make_int2(0, 0);
                 if (lane < nch) {
-                    const int2 t = ct[lane];
+                    const int2 mm = ct[lane];
+                    t.x = (mm.x & ~15) | (((mm.y + 16) & ~15) << 16);
                     nw = (uint32_t)(((t.x >> 16) - (t.x & 0xffff) + NCAP - 1) / NCAP);
                 }
                 uint32_t incl = nw;
@@ -396,7 +392,8 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 }
                 // entry table: entry j of the page -> (chunk, window)
                 if (lane < nch) {
-                    ct[lane].y = (int)((incl - nw) | (nw << 16));
+                    t.y = (int)((incl - nw) | (nw << 16));
+                    ct[lane] = t;
                     for (uint32_t w = 0; w < nw; ++w) ent[incl - nw + w] = (uint16_t)(lane | (w << 8));
                 }
                 nent = __shfl_sync(0xffffffffu, incl, 31);
@@ -426,6 +423,8 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             }
             return true;
         };
+        // page meta: fill, flags, item, the item's tile coordinates and problem,
+        // and the problem's reciprocal bandwidths
         auto close_page = [&](int flags, int64_t item, int tx, int ty, int tb, int pi, float ihs, float iht) {
             __syncwarp();
             if (lane == 0) {
