@@ -68,8 +68,12 @@ def lib():
         l.oracle_pb_boxes.argtypes = [P, dp, i64, dp, i64, dp, dp, dp]
         l.oracle_count_updates.argtypes = [P, dp, i64, dp]
         l.oracle_max_threads.argtypes = []
+        l.oracle_vb_adaptive.argtypes = [P, dp, dp, dp, i64, dp]
+        l.oracle_pb_adaptive.argtypes = [P, dp, dp, dp, i64, dp, dp]
+        l.oracle_pb_adaptive_boxes.argtypes = [P, dp, dp, dp, i64, dp, i64, dp, dp]
         for f in ("oracle_vb", "oracle_vb_voxels", "oracle_pb", "oracle_pb_box",
-                  "oracle_pb_boxes", "oracle_count_updates", "oracle_max_threads"):
+                  "oracle_pb_boxes", "oracle_count_updates", "oracle_max_threads",
+                  "oracle_vb_adaptive", "oracle_pb_adaptive", "oracle_pb_adaptive_boxes"):
             getattr(l, f).restype = ctypes.c_int
         _lib = l
     return _lib
@@ -158,3 +162,58 @@ def count_updates(points, p: Params) -> int:
     rc = lib().oracle_count_updates(ctypes.byref(p), _ptr(a), a.shape[0], c.ctypes.data)
     assert rc == 0
     return int(c[0])
+
+
+def _bw(a, n: int) -> np.ndarray:
+    b = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+    assert b.shape[0] == n, "one bandwidth per event"
+    return b
+
+
+def vb_adaptive(points, hs, ht, p: Params) -> np.ndarray:
+    """Algorithm 1 with per-event bandwidths hs[i], ht[i] (domain units) and
+    per-event normalisation 1/(n hs_i^2 ht_i); p.hs, p.ht unused."""
+    a = _pts(points)
+    h, t = _bw(hs, a.shape[0]), _bw(ht, a.shape[0])
+    out = np.empty((p.gx, p.gy, p.gt), dtype=np.float64)
+    rc = lib().oracle_vb_adaptive(ctypes.byref(p), _ptr(a), _ptr(h), _ptr(t), a.shape[0],
+                                  out.ctypes.data)
+    assert rc == 0
+    return out
+
+
+def pb_adaptive(points, hs, ht, p: Params, with_slack: bool = False):
+    """Algorithm 2 with per-event bandwidths (box per event); returns the grid, and
+    the binary32 tie slack when ``with_slack``."""
+    a = _pts(points)
+    h, t = _bw(hs, a.shape[0]), _bw(ht, a.shape[0])
+    out = np.empty((p.gx, p.gy, p.gt), dtype=np.float64)
+    slack = np.empty_like(out) if with_slack else None
+    rc = lib().oracle_pb_adaptive(ctypes.byref(p), _ptr(a), _ptr(h), _ptr(t), a.shape[0],
+                                  out.ctypes.data, slack.ctypes.data if with_slack else None)
+    assert rc == 0
+    return (out, slack) if with_slack else out
+
+
+def pb_adaptive_boxes(points, hs, ht, p: Params, boxes, with_slack: bool = True):
+    """Adaptive Algorithm 2 restricted to boxes; list of (values, slack)."""
+    a = _pts(points)
+    h, t = _bw(hs, a.shape[0]), _bw(ht, a.shape[0])
+    b = np.ascontiguousarray(np.asarray(boxes, dtype=np.int64).reshape(-1, 6))
+    sizes = (b[:, 1] - b[:, 0]) * (b[:, 3] - b[:, 2]) * (b[:, 5] - b[:, 4])
+    tot = int(sizes.sum())
+    out = np.empty(tot, dtype=np.float64)
+    slack = np.empty(tot, dtype=np.float64) if with_slack else None
+    rc = lib().oracle_pb_adaptive_boxes(ctypes.byref(p), _ptr(a), _ptr(h), _ptr(t), a.shape[0],
+                                        _ptr(b), b.shape[0], _ptr(out),
+                                        _ptr(slack) if with_slack else None)
+    assert rc == 0
+    res, off = [], 0
+    for j in range(b.shape[0]):
+        sz = int(sizes[j])
+        shape = (int(b[j, 1] - b[j, 0]), int(b[j, 3] - b[j, 2]), int(b[j, 5] - b[j, 4]))
+        v = out[off:off + sz].reshape(shape)
+        s_ = slack[off:off + sz].reshape(shape) if with_slack else None
+        res.append((v, s_))
+        off += sz
+    return res

@@ -316,3 +316,119 @@ int oracle_count_updates(const oracle_params* p, const double* pts, int64_t n, u
     *count = total;
     return 0;
 }
+
+/* ---------------------------------------------------- adaptive bandwidth --- */
+
+/* Per-event bandwidths, the generalisation the conclusion names as future work
+ * (a bandwidth that adapts to the local density of the population): event i
+ * carries its own hs_i, ht_i (domain units) and its own normalisation,
+ *
+ *   f(x,y,t) = 1/n * sum_{i : d_i < hs_i, |t - t_i| <= ht_i}
+ *                 k_s((x - x_i)/hs_i, (y - y_i)/hs_i) * k_t((t - t_i)/ht_i) / (hs_i^2 ht_i),
+ *
+ * so each event still contributes a separable cylinder of unit-scaled mass and
+ * every hs_i = hs, ht_i = ht gives the density above.  p->hs and p->ht are not
+ * used.  VB (Algorithm 1 with the per-event test) and PB (Algorithm 2 with a
+ * per-event box) are again written independently. */
+
+int oracle_vb_adaptive(const oracle_params* p, const double* pts, const double* hs,
+                       const double* ht, int64_t n, double* out) {
+    const int64_t G = p->gx * p->gy * p->gt;
+    if (n == 0) { memset(out, 0, sizeof(double) * (size_t)G); return 0; }
+    set_threads(p);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t X = 0; X < p->gx; ++X)
+        for (int64_t Y = 0; Y < p->gy; ++Y)
+            for (int64_t T = 0; T < p->gt; ++T) {
+                const double x = p->x0 + ((double)X + p->sample_off) * p->sres;
+                const double y = p->y0 + ((double)Y + p->sample_off) * p->sres;
+                const double t = p->t0 + ((double)T + p->sample_off) * p->tres;
+                double sum = 0.0;
+                for (int64_t i = 0; i < n; ++i) {
+                    double xi, yi, ti;
+                    event_domain(p, pts, i, &xi, &yi, &ti);
+                    const double d = sqrt((xi - x) * (xi - x) + (yi - y) * (yi - y));
+                    if (d < hs[i] && fabs(ti - t) <= ht[i])
+                        sum += k_s(p, (x - xi) / hs[i], (y - yi) / hs[i]) * k_t(p, (t - ti) / ht[i]) /
+                               (hs[i] * hs[i] * ht[i]);
+                }
+                out[(X * p->gy + Y) * p->gt + T] = sum / (double)n;
+            }
+    return 0;
+}
+
+/* PB with per-event bandwidths over the voxel box [bx0,bx1) x [by0,by1) x
+ * [bt0,bt1); slack as in pb_box, with the tie band on each event's own disk. */
+static void pb_box_adaptive(const oracle_params* p, const double* pts, const double* hs,
+                            const double* ht, int64_t n, int64_t bx0, int64_t bx1, int64_t by0,
+                            int64_t by1, int64_t bt0, int64_t bt1, double* box, double* slack) {
+    const int64_t ny = by1 - by0, nt = bt1 - bt0;
+    const size_t cells = (size_t)(bx1 - bx0) * (size_t)ny * (size_t)nt;
+    memset(box, 0, sizeof(double) * cells);
+    if (slack) memset(slack, 0, sizeof(double) * cells);
+    if (n == 0) return;
+    for (int64_t i = 0; i < n; ++i) {
+        const double hsv = hs[i] / p->sres, htv = ht[i] / p->tres;   /* bandwidths in voxels */
+        const double nrm = 1.0 / ((double)n * hs[i] * hs[i] * ht[i]);
+        double px, py, pt;
+        recentre(p, pts, i, &px, &py, &pt);
+        int64_t xa, xb, ya, yb, ta, tb;
+        if (!event_box(px, hsv, bx0, bx1 - 1, &xa, &xb)) continue;
+        if (!event_box(py, hsv, by0, by1 - 1, &ya, &yb)) continue;
+        if (!event_box(pt, htv, bt0, bt1 - 1, &ta, &tb)) continue;
+        for (int64_t X = xa; X <= xb; ++X) {
+            const double u = ((double)X + p->sample_off - px) / hsv;
+            for (int64_t Y = ya; Y <= yb; ++Y) {
+                const double v = ((double)Y + p->sample_off - py) / hsv;
+                const double s = u * u + v * v;
+                const int inside = s < 1.0;
+                const int tie = fabs(s - 1.0) <= TIE_BAND;
+                if (!inside && !tie) continue;
+                const double ks = k_s(p, u, v);
+                const size_t base = (size_t)(((X - bx0) * ny + (Y - by0)) * nt);
+                for (int64_t T = ta; T <= tb; ++T) {
+                    const double w = ((double)T + p->sample_off - pt) / htv;
+                    if (!(fabs(w) <= 1.0)) continue;
+                    const double term = ks * k_t(p, w) * nrm;
+                    if (inside) box[base + (size_t)(T - bt0)] += term;
+                    if (tie && slack) slack[base + (size_t)(T - bt0)] += fabs(term);
+                }
+            }
+        }
+    }
+}
+
+/* Full grid by adaptive PB; OpenMP over X planes as oracle_pb. */
+int oracle_pb_adaptive(const oracle_params* p, const double* pts, const double* hs,
+                       const double* ht, int64_t n, double* out, double* slack) {
+    set_threads(p);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t X = 0; X < p->gx; ++X) {
+        const size_t off = (size_t)X * (size_t)p->gy * (size_t)p->gt;
+        pb_box_adaptive(p, pts, hs, ht, n, X, X + 1, 0, p->gy, 0, p->gt, out + off,
+                        slack ? slack + off : NULL);
+    }
+    return 0;
+}
+
+/* Adaptive PB on a list of boxes (bx0, bx1, by0, by1, bt0, bt1). */
+int oracle_pb_adaptive_boxes(const oracle_params* p, const double* pts, const double* hs,
+                             const double* ht, int64_t n, const int64_t* boxes, int64_t nbox,
+                             double* out, double* slack) {
+    set_threads(p);
+    int64_t* offs = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nbox + 1));
+    if (!offs) return 1;
+    offs[0] = 0;
+    for (int64_t j = 0; j < nbox; ++j) {
+        const int64_t* b = boxes + 6 * j;
+        offs[j + 1] = offs[j] + (b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]);
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t j = 0; j < nbox; ++j) {
+        const int64_t* b = boxes + 6 * j;
+        pb_box_adaptive(p, pts, hs, ht, n, b[0], b[1], b[2], b[3], b[4], b[5], out + offs[j],
+                        slack ? slack + offs[j] : NULL);
+    }
+    free(offs);
+    return 0;
+}
