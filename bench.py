@@ -14,7 +14,9 @@ Under torchrun every rank computes its own instance (seed offset = rank): the
 instances are independent, so scaling is weak and no collective touches the
 data; the only collectives are the barrier and the max-over-ranks of the time.
 ``--impl reference`` times the FP64 CPU oracle (the paper has no GPU code) on a
-bounded sample of tiles of the same workload.
+bounded sample of tiles of the same workload.  ``--bandwidth adaptive`` gives
+every event its own bandwidths (log-uniform in [h/spread, h*spread] around the
+workload's pair) and times stkde_compute_adaptive instead.
 """
 from __future__ import annotations
 
@@ -58,7 +60,18 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--bandwidth", choices=["fixed", "adaptive"], default="fixed",
+                    help="adaptive: per-event bandwidths log-uniform in [h/spread, h*spread]")
+    ap.add_argument("--spread", type=float, default=2.0)
     return ap.parse_args()
+
+
+def workload_bandwidths(args, w, seed):
+    """(name, hs, ht): the workload's fixed pair, or per-event arrays."""
+    if args.bandwidth == "fixed":
+        return w.name, w.hs, w.ht
+    hs, ht = synth.adaptive_bandwidths(w.n, w.hs, w.ht, spread=args.spread, seed=seed)
+    return f"{w.name}-adaptive-x{args.spread:g}", hs, ht
 
 
 def load_peaks():
@@ -143,10 +156,10 @@ def tile_boxes(w, seed=0):
              min(w.gy, int(c % ny) * 8 + 8), 0, w.gt) for c in order]
 
 
-def oracle_sample(w, seconds, seed=0, calib=None):
+def oracle_sample(w, seconds, seed=0, calib=None, bw=None):
     """Times the FP64 oracle (Algorithm 2 on random tiles, all host cores) for
     about `seconds`, growing the sample in batches; returns (pairs, elapsed,
-    boxes, results, seconds per box)."""
+    boxes, results, seconds per box).  bw: per-event (hs, ht) arrays or None."""
     import oracle
     p = oracle.params(w.gx, w.gy, w.gt, w.hs, w.ht, x0=w.x0, y0=w.y0, t0=w.t0, sres=w.sres,
                       tres=w.tres)
@@ -160,7 +173,11 @@ def oracle_sample(w, seconds, seed=0, calib=None):
             k = int(max(1, round((seconds - elapsed) / max(per_box, 1e-6))))
         sel = boxes[done:done + k]
         t = time.perf_counter()
-        r, c = oracle.pb_boxes(w.points, p, sel, with_slack=True, pair_counts=True)
+        if bw is None:
+            r, c = oracle.pb_boxes(w.points, p, sel, with_slack=True, pair_counts=True)
+        else:
+            r, c = oracle.pb_adaptive_boxes(w.points, bw[0], bw[1], p, sel, with_slack=True,
+                                            pair_counts=True)
         dt = time.perf_counter() - t
         res.extend(r)
         pairs += int(c.sum())
@@ -179,13 +196,15 @@ def run_reference(args):
     import oracle
     oracle.build()
     w = synth.WORKLOADS[args.workload]()
+    name, hs, ht = workload_bandwidths(args, w, 0)
+    bw = None if args.bandwidth == "fixed" else (hs, ht)
     total_budget = 150.0
     per_step = max(1.0, total_budget / max(1, args.steps + args.warmup))
-    _, _, _, _, per_box = oracle_sample(w, 0.5)
+    _, _, _, _, per_box = oracle_sample(w, 0.5, bw=bw)
     vals = []
     ntiles = []
     for i in range(args.warmup + args.steps):
-        pairs, dt, sel, _, _ = oracle_sample(w, per_step, seed=i, calib=per_box)
+        pairs, dt, sel, _, _ = oracle_sample(w, per_step, seed=i, calib=per_box, bw=bw)
         if i >= args.warmup:
             vals.append((pairs, dt))
             ntiles.append(len(sel))
@@ -195,14 +214,14 @@ def run_reference(args):
     cores = oracle.max_threads()
     tiles = int(round(statistics.mean(ntiles)))
     sample = (f"FP64 oracle (Algorithm 2) on {tiles} random 16x8x{w.gt} tiles per step of the "
-              f"{w.name} workload, {cores} host threads")
+              f"{name} workload, {cores} host threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / len(vals),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "grid": [w.gx, w.gy, w.gt], "hs": w.hs,
-                   "ht": w.ht, "sample": "tiles"},
+        "config": {"workload": name, "n": w.n, "grid": [w.gx, w.gy, w.gt], "hs": w.hs,
+                   "ht": w.ht, "bandwidth": args.bandwidth, "sample": "tiles"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -217,7 +236,7 @@ def recorded_traffic(args):
     """DRAM bytes (read + write) of one tile-kernel launch from the committed ncu
     summary, if it was taken on this workload and form with the current kernel
     source; else None."""
-    if args.workload != "large" or args.form != "bf16x3":
+    if args.workload != "large" or args.form != "bf16x3" or args.bandwidth != "fixed":
         return None
     import hashlib
     prof = os.path.join(ROOT, "profiles", "tile_tc_large_dram.md")
@@ -275,18 +294,30 @@ def run_ours(args):
 
     peaks, peaks_src = load_peaks()
     w = synth.WORKLOADS[args.workload](seed_offset=rank)
+    wname, hs_h, ht_h = workload_bandwidths(args, w, rank)
+    adaptive = args.bandwidth == "adaptive"
     dims = (w.gx, w.gy, w.gt)
     stream = torch.cuda.current_stream(dev)
     pts = torch.from_numpy(w.points).to(dev)
+    hs_d = torch.from_numpy(hs_h).to(dev) if adaptive else w.hs
+    ht_d = torch.from_numpy(ht_h).to(dev) if adaptive else w.ht
     out = torch.empty(dims, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    def compute(c, p, o, hs=hs_d, ht=ht_d):
+        if adaptive:
+            return c.compute_adaptive(p, dims, hs, ht, out=o)
+        return c.compute(p, dims, hs, ht, out=o)
+
     ctx = pkg.Context(device=local, stream=stream, form=args.form, profile=False)
-    updates = ctx.count_updates(pts, dims, w.hs, w.ht)
+    if adaptive:
+        updates = ctx.count_updates_adaptive(pts, dims, hs_d, ht_d)
+    else:
+        updates = ctx.count_updates(pts, dims, w.hs, w.ht)
 
     # ---- timed steps: device-resident inputs, L2 flushed before each step
     for _ in range(args.warmup):
-        ctx.compute(pts, dims, w.hs, w.ht, out=out)
+        compute(ctx, pts, out)
     ctx.synchronize()
     launches_per_step = ctx.last_launch_count()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -298,7 +329,7 @@ def run_ours(args):
     for i in range(args.steps):
         flush.fill_(float(i))
         starts[i].record(stream)
-        ctx.compute(pts, dims, w.hs, w.ht, out=out)
+        compute(ctx, pts, out)
         ends[i].record(stream)
     barrier()
     clk = clocks.stop() if rank == 0 else None
@@ -314,7 +345,7 @@ def run_ours(args):
     phases = []
     for i in range(args.steps):
         flush.fill_(float(i))
-        pctx.compute(pts, dims, w.hs, w.ht, out=out)
+        compute(pctx, pts, out)
         phases.append(pctx.phase_times())
     pctx.synchronize()
     pctx.close()
@@ -353,17 +384,20 @@ def run_ours(args):
     if args.e2e_steps > 0:
         hpts = torch.from_numpy(w.points).pin_memory()
         hout = torch.empty(dims, dtype=torch.float32, pin_memory=True)
-        ctx.compute(hpts, dims, w.hs, w.ht, out=hout)
+        hhs = torch.from_numpy(hs_h).pin_memory() if adaptive else w.hs
+        hht = torch.from_numpy(ht_h).pin_memory() if adaptive else w.ht
+        h2d = int(w.points.nbytes) + (int(hs_h.nbytes + ht_h.nbytes) if adaptive else 0)
+        compute(ctx, hpts, hout, hhs, hht)
         ctx.synchronize()
         barrier()
         t = time.perf_counter()
         for _ in range(args.e2e_steps):
-            ctx.compute(hpts, dims, w.hs, w.ht, out=hout)
+            compute(ctx, hpts, hout, hhs, hht)
             ctx.synchronize()
         barrier()
         e2e_s = max_over_ranks(time.perf_counter() - t)
         e2e = {"value": sum_over_ranks(float(updates) * args.e2e_steps) / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": int(w.points.nbytes), "d2h_bytes_per_step": grid_bytes,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": grid_bytes,
                "ms_per_step": 1e3 * e2e_s / args.e2e_steps}
         del hout, hpts
 
@@ -371,18 +405,19 @@ def run_ours(args):
     forms = {args.form: {"ms_per_grid": ms_per_step, "updates_per_s": value / max(world, 1),
                          "tile_kernel_ms": tile_ms}}
     if rank == 0 and world == 1 and args.compare:
-        for f in [x for x in args.compare.split(",") if x and x != args.form]:
+        for f in [x for x in args.compare.split(",")
+                  if x and x != args.form and not (adaptive and x == "scatter")]:
             fo = torch.empty(dims, dtype=torch.float32, device=dev)
             with pkg.Context(device=local, stream=stream, form=f) as fc:
                 reps = 1 if f == "scatter" else 3
-                fc.compute(pts, dims, w.hs, w.ht, out=fo)
+                compute(fc, pts, fo)
                 fc.synchronize()
                 s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 tot = 0.0
                 for i in range(reps):
                     flush.fill_(float(i))
                     s0.record(stream)
-                    fc.compute(pts, dims, w.hs, w.ht, out=fo)
+                    compute(fc, pts, fo)
                     s1.record(stream)
                     fc.synchronize()
                     tot += s0.elapsed_time(s1)
@@ -394,11 +429,12 @@ def run_ours(args):
     errs = {}
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
-        pairs, dt, boxes, res, _ = oracle_sample(w, args.cpu_seconds, seed=rank)
+        pairs, dt, boxes, res, _ = oracle_sample(w, args.cpu_seconds, seed=rank,
+                                                 bw=(hs_h, ht_h) if adaptive else None)
         cores = oracle.max_threads()
         cpu = {"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"FP64 oracle (Algorithm 2) on {len(boxes)} random 16x8x{w.gt} tiles "
-                         f"of the {w.name} workload ({pairs} updates, {dt:.1f} s)"}
+                         f"of the {wname} workload ({pairs} updates, {dt:.1f} s)"}
         scale = max(r.max() for r, _ in res)
         for f, buf in [(args.form, out)] + [(k, v["_out"]) for k, v in forms.items() if "_out" in v]:
             worst = 0.0
@@ -419,8 +455,10 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"bf16x3": "bf16", "fp16x3": "f16", "fp32": "f32", "scatter": "f32"}[args.form],
             "data": "synthetic",
-            "config": {"workload": w.name, "n": w.n, "grid": [w.gx, w.gy, w.gt], "hs": w.hs,
-                       "ht": w.ht, "form": args.form, "updates_per_grid": updates,
+            "config": {"workload": wname, "n": w.n, "grid": [w.gx, w.gy, w.gt], "hs": w.hs,
+                       "ht": w.ht, "bandwidth": args.bandwidth if not adaptive else
+                       f"per event, log-uniform in [h/{args.spread:g}, h*{args.spread:g}]",
+                       "form": args.form, "updates_per_grid": updates,
                        "l2": "flushed before each step (256 MiB write); output 2.1 GB > L2",
                        "parallelism": f"{world} independent instance(s), one per GPU"},
             "roofline": roof,

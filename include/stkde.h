@@ -143,12 +143,38 @@ typedef struct {
  * 2^32 bins or 2^31 tiles or more), OOM, CUDA.  count = 0 is a no-op. */
 STKDE_API stkde_status stkde_compute_batch(stkde_ctx* ctx, const stkde_problem* problems, int count);
 
+/* The Section 2.1 density with one bandwidth pair per event, the bandwidth that
+ * adapts to the local population density which Section 8 (Conclusion) names as
+ * future work; the caller chooses the bandwidths.  Event i adds
+ *     k_s((x - x_i)/hs[i], (y - y_i)/hs[i]) k_t((t - t_i)/ht[i]) / (n hs[i]^2 ht[i])
+ * to every voxel inside its own cylinder (spatial test strict, temporal
+ * inclusive), so hs[i] = hs, ht[i] = ht for all i gives stkde_compute's density.
+ * hs, ht: n doubles each, domain units, host or device memory (each on its
+ * own); points, grid and out as in stkde_compute.  Event binning and tile reach
+ * use the largest bandwidths, so a few very large ones slow every tile.  With
+ * device bandwidth arrays the call waits for the stream once, to read their
+ * range.  Errors: INVALID_ARGUMENT (as stkde_compute; a NULL hs or ht with
+ * n > 0; a bandwidth that is not finite and positive, or hs[i]/sres or
+ * ht[i]/tres >= 1e6), UNSUPPORTED (the scatter form; the fp16x3 form when
+ * (max hs / min hs)^2 (max ht / min ht) > 2^14, where its weighted operand
+ * would leave the fp16 range), OOM, CUDA.  n = 0 writes zeros. */
+STKDE_API stkde_status stkde_compute_adaptive(stkde_ctx* ctx, const double* points, int64_t n,
+                                              const stkde_grid* grid, const double* hs,
+                                              const double* ht, float* out);
+
 /* Number of (event, in-grid voxel) pairs inside the bandwidth cylinder
  * (spatial test strict, temporal inclusive): the voxel-point updates of the
  * problem.  Synchronous; FP64 arithmetic on the re-centred binary32 events. */
 STKDE_API stkde_status stkde_count_updates(stkde_ctx* ctx, const double* points, int64_t n,
                                  const stkde_grid* grid, double hs, double ht,
                                  uint64_t* count);
+
+/* stkde_count_updates with per-event bandwidths hs, ht (as in
+ * stkde_compute_adaptive): the pairs inside each event's own cylinder.
+ * Synchronous.  Errors as stkde_compute_adaptive's INVALID_ARGUMENT cases. */
+STKDE_API stkde_status stkde_count_updates_adaptive(stkde_ctx* ctx, const double* points, int64_t n,
+                                                    const stkde_grid* grid, const double* hs,
+                                                    const double* ht, uint64_t* count);
 
 /* Waits for the context's stream and returns the first latched device error,
  * clearing it. */

@@ -70,7 +70,7 @@ def lib():
         l.oracle_max_threads.argtypes = []
         l.oracle_vb_adaptive.argtypes = [P, dp, dp, dp, i64, dp]
         l.oracle_pb_adaptive.argtypes = [P, dp, dp, dp, i64, dp, dp]
-        l.oracle_pb_adaptive_boxes.argtypes = [P, dp, dp, dp, i64, dp, i64, dp, dp]
+        l.oracle_pb_adaptive_boxes.argtypes = [P, dp, dp, dp, i64, dp, i64, dp, dp, dp]
         for f in ("oracle_vb", "oracle_vb_voxels", "oracle_pb", "oracle_pb_box",
                   "oracle_pb_boxes", "oracle_count_updates", "oracle_max_threads",
                   "oracle_vb_adaptive", "oracle_pb_adaptive", "oracle_pb_adaptive_boxes"):
@@ -195,8 +195,10 @@ def pb_adaptive(points, hs, ht, p: Params, with_slack: bool = False):
     return (out, slack) if with_slack else out
 
 
-def pb_adaptive_boxes(points, hs, ht, p: Params, boxes, with_slack: bool = True):
-    """Adaptive Algorithm 2 restricted to boxes; list of (values, slack)."""
+def pb_adaptive_boxes(points, hs, ht, p: Params, boxes, with_slack: bool = True,
+                      pair_counts: bool = False):
+    """Adaptive Algorithm 2 restricted to boxes; list of (values, slack), plus the
+    per-box count of in-cylinder pairs when ``pair_counts``."""
     a = _pts(points)
     h, t = _bw(hs, a.shape[0]), _bw(ht, a.shape[0])
     b = np.ascontiguousarray(np.asarray(boxes, dtype=np.int64).reshape(-1, 6))
@@ -204,9 +206,10 @@ def pb_adaptive_boxes(points, hs, ht, p: Params, boxes, with_slack: bool = True)
     tot = int(sizes.sum())
     out = np.empty(tot, dtype=np.float64)
     slack = np.empty(tot, dtype=np.float64) if with_slack else None
+    npairs = np.zeros(b.shape[0], dtype=np.uint64)
     rc = lib().oracle_pb_adaptive_boxes(ctypes.byref(p), _ptr(a), _ptr(h), _ptr(t), a.shape[0],
                                         _ptr(b), b.shape[0], _ptr(out),
-                                        _ptr(slack) if with_slack else None)
+                                        _ptr(slack) if with_slack else None, _ptr(npairs))
     assert rc == 0
     res, off = [], 0
     for j in range(b.shape[0]):
@@ -216,4 +219,4 @@ def pb_adaptive_boxes(points, hs, ht, p: Params, boxes, with_slack: bool = True)
         s_ = slack[off:off + sz].reshape(shape) if with_slack else None
         res.append((v, s_))
         off += sz
-    return res
+    return (res, npairs) if pair_counts else res

@@ -361,12 +361,15 @@ int oracle_vb_adaptive(const oracle_params* p, const double* pts, const double* 
  * [bt0,bt1); slack as in pb_box, with the tie band on each event's own disk. */
 static void pb_box_adaptive(const oracle_params* p, const double* pts, const double* hs,
                             const double* ht, int64_t n, int64_t bx0, int64_t bx1, int64_t by0,
-                            int64_t by1, int64_t bt0, int64_t bt1, double* box, double* slack) {
+                            int64_t by1, int64_t bt0, int64_t bt1, double* box, double* slack,
+                            uint64_t* npairs) {
     const int64_t ny = by1 - by0, nt = bt1 - bt0;
     const size_t cells = (size_t)(bx1 - bx0) * (size_t)ny * (size_t)nt;
     memset(box, 0, sizeof(double) * cells);
     if (slack) memset(slack, 0, sizeof(double) * cells);
+    if (npairs) *npairs = 0;
     if (n == 0) return;
+    uint64_t pairs = 0;
     for (int64_t i = 0; i < n; ++i) {
         const double hsv = hs[i] / p->sres, htv = ht[i] / p->tres;   /* bandwidths in voxels */
         const double nrm = 1.0 / ((double)n * hs[i] * hs[i] * ht[i]);
@@ -392,10 +395,12 @@ static void pb_box_adaptive(const oracle_params* p, const double* pts, const dou
                     const double term = ks * k_t(p, w) * nrm;
                     if (inside) box[base + (size_t)(T - bt0)] += term;
                     if (tie && slack) slack[base + (size_t)(T - bt0)] += fabs(term);
+                    pairs += (uint64_t)inside;
                 }
             }
         }
     }
+    if (npairs) *npairs = pairs;
 }
 
 /* Full grid by adaptive PB; OpenMP over X planes as oracle_pb. */
@@ -406,15 +411,16 @@ int oracle_pb_adaptive(const oracle_params* p, const double* pts, const double* 
     for (int64_t X = 0; X < p->gx; ++X) {
         const size_t off = (size_t)X * (size_t)p->gy * (size_t)p->gt;
         pb_box_adaptive(p, pts, hs, ht, n, X, X + 1, 0, p->gy, 0, p->gt, out + off,
-                        slack ? slack + off : NULL);
+                        slack ? slack + off : NULL, NULL);
     }
     return 0;
 }
 
-/* Adaptive PB on a list of boxes (bx0, bx1, by0, by1, bt0, bt1). */
+/* Adaptive PB on a list of boxes (bx0, bx1, by0, by1, bt0, bt1); npairs[j], if
+ * given, receives the in-cylinder (event, voxel) pairs of box j. */
 int oracle_pb_adaptive_boxes(const oracle_params* p, const double* pts, const double* hs,
                              const double* ht, int64_t n, const int64_t* boxes, int64_t nbox,
-                             double* out, double* slack) {
+                             double* out, double* slack, uint64_t* npairs) {
     set_threads(p);
     int64_t* offs = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nbox + 1));
     if (!offs) return 1;
@@ -427,7 +433,7 @@ int oracle_pb_adaptive_boxes(const oracle_params* p, const double* pts, const do
     for (int64_t j = 0; j < nbox; ++j) {
         const int64_t* b = boxes + 6 * j;
         pb_box_adaptive(p, pts, hs, ht, n, b[0], b[1], b[2], b[3], b[4], b[5], out + offs[j],
-                        slack ? slack + offs[j] : NULL);
+                        slack ? slack + offs[j] : NULL, npairs ? npairs + j : NULL);
     }
     free(offs);
     return 0;

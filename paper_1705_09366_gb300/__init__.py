@@ -47,6 +47,7 @@ EXPORTED_SYMBOLS = (
     "stkde_default_options", "stkde_create", "stkde_compute", "stkde_compute_batch",
     "stkde_count_updates", "stkde_synchronize", "stkde_phase_times", "stkde_destroy",
     "stkde_status_string", "stkde_last_launch_count", "stkde_compute_static",
+    "stkde_compute_adaptive", "stkde_count_updates_adaptive",
 )
 
 STATIC_MAX_EVENTS = 262144
@@ -95,6 +96,11 @@ def lib():
         l.stkde_compute.argtypes = [vp, vp, i64, ctypes.POINTER(Grid), dbl, dbl, vp]
         l.stkde_compute.restype = ctypes.c_int
         l.stkde_compute_batch.argtypes = [vp, ctypes.POINTER(Problem), ctypes.c_int]
+        l.stkde_compute_adaptive.argtypes = [vp, vp, i64, ctypes.POINTER(Grid), vp, vp, vp]
+        l.stkde_compute_adaptive.restype = ctypes.c_int
+        l.stkde_count_updates_adaptive.argtypes = [vp, vp, i64, ctypes.POINTER(Grid), vp, vp,
+                                                   ctypes.POINTER(ctypes.c_uint64)]
+        l.stkde_count_updates_adaptive.restype = ctypes.c_int
         l.stkde_compute_batch.restype = ctypes.c_int
         l.stkde_count_updates.argtypes = [vp, vp, i64, ctypes.POINTER(Grid), dbl, dbl,
                                           ctypes.POINTER(ctypes.c_uint64)]
@@ -180,6 +186,21 @@ def stkde_compute(ctx, points, n: int, grid: Grid, hs: float, ht: float, out) ->
                                float(ht), _ptr(out)), "stkde_compute")
 
 
+def stkde_compute_adaptive(ctx, points, n: int, grid: Grid, hs, ht, out) -> None:
+    """Per-event bandwidths: ``hs``, ``ht`` hold n float64 values each (domain
+    units, host or device)."""
+    _check(lib().stkde_compute_adaptive(ctx, _ptr(points), int(n), ctypes.byref(grid), _ptr(hs),
+                                        _ptr(ht), _ptr(out)), "stkde_compute_adaptive")
+
+
+def stkde_count_updates_adaptive(ctx, points, n: int, grid: Grid, hs, ht) -> int:
+    c = ctypes.c_uint64(0)
+    _check(lib().stkde_count_updates_adaptive(ctx, _ptr(points), int(n), ctypes.byref(grid),
+                                              _ptr(hs), _ptr(ht), ctypes.byref(c)),
+           "stkde_count_updates_adaptive")
+    return int(c.value)
+
+
 def stkde_compute_batch(ctx, problems) -> None:
     arr = (Problem * len(problems))(*problems)
     _check(lib().stkde_compute_batch(ctx, arr, len(problems)), "stkde_compute_batch")
@@ -260,6 +281,27 @@ class Context:
         g = make_grid(gx, gy, gt, *origin, sres=sres, tres=tres)
         stkde_compute(self.handle, points, n, g, hs, ht, out)
         return out
+
+    def compute_adaptive(self, points, dims, hs, ht, out=None, origin=(0.0, 0.0, 0.0), sres=1.0,
+                         tres=1.0):
+        """Density with per-event bandwidths ``hs``, ``ht`` ((n,) float64 each,
+        domain units); otherwise as :meth:`compute`."""
+        gx, gy, gt = (int(d) for d in dims)
+        if out is None:
+            import torch
+            out = torch.empty((gx, gy, gt), dtype=torch.float32, device=f"cuda:{self.device}")
+        n = int(points.shape[0])
+        for a in (hs, ht):
+            if int(a.shape[0]) != n:
+                raise ValueError("one bandwidth per event")
+        g = make_grid(gx, gy, gt, *origin, sres=sres, tres=tres)
+        stkde_compute_adaptive(self.handle, points, n, g, hs, ht, out)
+        return out
+
+    def count_updates_adaptive(self, points, dims, hs, ht, origin=(0.0, 0.0, 0.0), sres=1.0,
+                               tres=1.0):
+        g = make_grid(*dims, *origin, sres=sres, tres=tres)
+        return stkde_count_updates_adaptive(self.handle, points, int(points.shape[0]), g, hs, ht)
 
     def compute_batch(self, problems):
         """Densities of several independent problems in one batched call.

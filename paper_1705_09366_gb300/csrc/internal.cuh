@@ -51,12 +51,19 @@ struct ProblemDev {
     const float4* ev;         // the batch's events sorted by key
     const uint32_t* start;    // the problem's bin boundaries start[0 .. nkeys]
     float* out;               // the problem's output grid, device memory
+    const float4* evp;        // per-event bandwidths in sorted order (NULL: the plan's)
 };
 
 // Per-problem device buffers (views into the context's workspace).
 struct Bins {
     const float4* ev;        // re-centred events sorted by key: (x', y', t', bits(original index))
     const uint32_t* start;   // start[k] = first sorted position with key >= k, k in [0, nkeys]
+    // Per-event bandwidths in the same sorted order, (hsv_i, htv_i, 1/hsv_i,
+    // 1/htv_i) in voxels, or NULL when every event takes the plan's.  With
+    // per-event bandwidths the plan holds the largest ones (binning, tile reach
+    // and the normalisation 1/(n hs_max^2 ht_max)); event i's terms are weighted
+    // by (hs_max/hs_i)^2 (ht_max/ht_i).
+    const float4* evp = nullptr;
 };
 
 // ----------------------------------------------------------------- prep.cu
@@ -72,9 +79,22 @@ void launch_radix_sort(uint32_t* keys, uint32_t* idx, uint32_t* keys_tmp, uint32
 void launch_bounds_gather(const uint32_t* sorted_keys, const uint32_t* sorted_idx,
                           const float4* ev, int n, uint32_t nkeys, uint32_t* start,
                           float4* ev_sorted, cudaStream_t st);
-// Exact update count (FP64 on the binary32 re-centred events).
-// hsv, htv: FP64 bandwidths in voxels.
+// Per-event bandwidths (domain units, n doubles each, device memory) to the
+// (hsv, htv, 1/hsv, 1/htv) records of Bins::evp, in input order (FP64, rounded once).
+void launch_bandwidths(const double* hs, const double* ht, int n, double sres, double tres,
+                       float4* evp, cudaStream_t st);
+// range[0..2] = bits of the smallest and largest of h[0..n) (n doubles, device
+// memory), and a nonzero word if one is not finite and positive.  range must be
+// preset to {~0, 0, 0}.
+void launch_bandwidth_range(const double* h, int n, unsigned long long* range, cudaStream_t st);
+// ev_sorted[p] = ev[idx[p]] (the gather of launch_bounds_gather, for a second array).
+void launch_gather(const uint32_t* sorted_idx, const float4* ev, int n, float4* ev_sorted,
+                   cudaStream_t st);
+// Exact update count (FP64 on the binary32 re-centred events, in input order).
+// hsv, htv: FP64 bandwidths in voxels; or per-event bandwidths hs, ht (domain
+// units, device memory, n each; NULL for the fixed pair) divided by sres, tres.
 void launch_count_updates(const float4* ev, int n, const Plan& pl, double hsv, double htv,
+                          const double* hs, const double* ht, double sres, double tres,
                           unsigned long long* count, cudaStream_t st);
 
 // ------------------------------------------------------------ tile_fp32.cu

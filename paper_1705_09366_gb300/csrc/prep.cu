@@ -275,6 +275,61 @@ void launch_bounds_gather(const uint32_t* sorted_keys, const uint32_t* sorted_id
     if (n > 0) k_gather<<<(n + 255) / 256, 256, 0, st>>>(sorted_idx, ev, n, ev_sorted);
 }
 
+void launch_gather(const uint32_t* sorted_idx, const float4* ev, int n, float4* ev_sorted,
+                   cudaStream_t st) {
+    if (n > 0) k_gather<<<(n + 255) / 256, 256, 0, st>>>(sorted_idx, ev, n, ev_sorted);
+}
+
+// ----------------------------------------------- per-event bandwidths ---
+// Adaptive bandwidths (the density-dependent bandwidth the conclusion names as
+// future work): event i carries its own hs_i, ht_i.  Converted once to voxels in
+// FP64 as the plan converts the fixed ones, then rounded.
+
+__global__ void k_bandwidths(const double* __restrict__ hs, const double* __restrict__ ht, int n,
+                             double sres, double tres, float4* __restrict__ evp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double h = hs[i], k = ht[i];
+    evp[i] = make_float4(__double2float_rn(h / sres), __double2float_rn(k / tres),
+                         __double2float_rn(sres / h), __double2float_rn(tres / k));
+}
+
+void launch_bandwidths(const double* hs, const double* ht, int n, double sres, double tres,
+                       float4* evp, cudaStream_t st) {
+    if (n > 0) k_bandwidths<<<(n + 255) / 256, 256, 0, st>>>(hs, ht, n, sres, tres, evp);
+}
+
+// Positive finite doubles order as their bit patterns, so the extrema are
+// unsigned integer min/max of the bits.
+__global__ void k_bandwidth_range(const double* __restrict__ h, int n,
+                                  unsigned long long* __restrict__ range) {
+    unsigned long long lo = ~0ull, hi = 0, bad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = h[i];
+        if (!(isfinite(v) && v > 0.0)) { bad = 1; continue; }
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        lo = min(lo, b);
+        hi = max(hi, b);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&range[0], lo);
+        atomicMax(&range[1], hi);
+        if (bad) atomicOr(&range[2], bad);
+    }
+}
+
+void launch_bandwidth_range(const double* h, int n, unsigned long long* range, cudaStream_t st) {
+    if (n <= 0) return;
+    int blocks = (n + 255) / 256;
+    blocks = blocks < 1024 ? blocks : 1024;
+    k_bandwidth_range<<<blocks, 256, 0, st>>>(h, n, range);
+}
+
 // --------------------------------------------------------- update count ---
 // Exact count of (event, in-grid voxel) pairs inside the cylinder, FP64 on the
 // binary32 events.  Per event: the T count times the xy count; along each X row
@@ -286,12 +341,16 @@ __device__ __forceinline__ bool inside_xy(double du, double py, int Y, double hs
     return du * du + dv * dv < 1.0;
 }
 
-__global__ void k_count(const float4* __restrict__ ev, int n, int gx, int gy, int gt, double hs,
-                        double ht, unsigned long long* __restrict__ count) {
+__global__ void k_count(const float4* __restrict__ ev, int n, int gx, int gy, int gt, double hs0,
+                        double ht0, const double* __restrict__ hs_i, const double* __restrict__ ht_i,
+                        double sres, double tres, unsigned long long* __restrict__ count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long c = 0;
     if (i < n) {
         const float4 e = ev[i];
+        // per-event bandwidths in voxels (events are in input order here)
+        const double hs = hs_i ? hs_i[i] / sres : hs0;
+        const double ht = ht_i ? ht_i[i] / tres : ht0;
         const double px = e.x, py = e.y, pt = e.z;
         if (isfinite(px) && isfinite(py) && isfinite(pt) && fabs(px) < 1e9 && fabs(py) < 1e9 &&
             fabs(pt) < 1e9) {
@@ -327,9 +386,11 @@ __global__ void k_count(const float4* __restrict__ ev, int n, int gx, int gy, in
 }
 
 void launch_count_updates(const float4* ev, int n, const Plan& pl, double hsv, double htv,
+                          const double* hs, const double* ht, double sres, double tres,
                           unsigned long long* count, cudaStream_t st) {
     if (n <= 0) return;
-    k_count<<<(n + 255) / 256, 256, 0, st>>>(ev, n, pl.gx, pl.gy, pl.gt, hsv, htv, count);
+    k_count<<<(n + 255) / 256, 256, 0, st>>>(ev, n, pl.gx, pl.gy, pl.gt, hsv, htv, hs, ht, sres,
+                                             tres, count);
 }
 
 }  // namespace stkde

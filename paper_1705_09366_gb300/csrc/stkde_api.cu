@@ -34,6 +34,7 @@ struct stkde_ctx {
     int* d_err = nullptr;
     int* d_ctr = nullptr;  // tile queue of the tensor tile kernel
     unsigned long long* d_count = nullptr;
+    unsigned long long* d_range = nullptr;  // bandwidth range of stkde_compute_adaptive (2 x 3 words)
     cudaEvent_t ev[MAX_PHASES + 1];
     int nphase = 0;
     bool events_ok = false;
@@ -164,9 +165,11 @@ void mark(stkde_ctx* c) {
 }
 
 // Enqueues one problem whose events are already on the device.  The result goes
-// to the device buffer `out`.
+// to the device buffer `out`.  With per-event bandwidths, evp holds their
+// records in input order and evp_sorted receives them in bin order.
 stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stkde_grid* g,
-                     const Workspace& w, float* out) {
+                     const Workspace& w, float* out, const float4* evp = nullptr,
+                     float4* evp_sorted = nullptr) {
     cudaStream_t st = c->stream;
     const int form = c->opt.form;
     const int n = pl.n;
@@ -190,8 +193,12 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
     mark(c);
     launch_bounds_gather(w.keys, w.idx, w.ev, n, pl.nkeys, w.start, w.ev_sorted, st);
     c->launches += 2;
+    if (evp) {
+        launch_gather(w.idx, evp, n, evp_sorted, st);
+        c->launches += 1;
+    }
     mark(c);
-    Bins b{w.ev_sorted, w.start};
+    Bins b{w.ev_sorted, w.start, evp ? evp_sorted : nullptr};
     if (form == STKDE_FORM_FP32) {
         launch_tile_fp32(pl, b, out, c->d_err, st);
     } else {
@@ -204,6 +211,45 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
     c->launches += 1;
     mark(c);
     return cuda_status(cudaGetLastError());
+}
+
+// Smallest and largest of the per-event bandwidth arrays hs, ht (kind 1: device
+// memory, read by a reduction kernel and one wait for the stream; else host
+// memory, read here); INVALID_ARGUMENT if one is not finite and positive.
+stkde_status bandwidth_range(stkde_ctx* c, int64_t n, const double* hs, const double* ht,
+                             int hkind, int tkind, double lo[2], double hi[2]) {
+    const double* arr[2] = {hs, ht};
+    const int kind[2] = {hkind, tkind};
+    bool bad = false;
+    if (hkind == 1 || tkind == 1) {
+        unsigned long long init[6] = {~0ull, 0ull, 0ull, ~0ull, 0ull, 0ull};
+        cudaError_t e = cudaMemcpyAsync(c->d_range, init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        for (int a = 0; a < 2; ++a)
+            if (kind[a] == 1) launch_bandwidth_range(arr[a], (int)n, c->d_range + 3 * a, c->stream);
+        unsigned long long got[6];
+        e = cudaMemcpyAsync(got, c->d_range, sizeof(got), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        for (int a = 0; a < 2; ++a) {
+            if (kind[a] != 1) continue;
+            bad = bad || got[3 * a + 2] != 0;
+            memcpy(&lo[a], &got[3 * a], sizeof(double));
+            memcpy(&hi[a], &got[3 * a + 1], sizeof(double));
+        }
+    }
+    for (int a = 0; a < 2; ++a) {
+        if (kind[a] == 1) continue;
+        lo[a] = INFINITY;
+        hi[a] = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            const double v = arr[a][i];
+            if (!finite_pos(v)) { bad = true; break; }
+            lo[a] = v < lo[a] ? v : lo[a];
+            hi[a] = v > hi[a] ? v : hi[a];
+        }
+    }
+    return bad ? STKDE_ERR_INVALID_ARGUMENT : STKDE_OK;
 }
 
 }  // namespace
@@ -269,10 +315,12 @@ stkde_status stkde_create(stkde_ctx** out, const stkde_options* opt) {
     c->sm_count = prop.multiProcessorCount;
     if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&c->d_ctr, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc(&c->d_count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_range, 6 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         if (c->d_err) cudaFree(c->d_err);
         if (c->d_ctr) cudaFree(c->d_ctr);
+        if (c->d_count) cudaFree(c->d_count);
         delete c;
         return STKDE_ERR_OOM;
     }
@@ -294,6 +342,7 @@ void stkde_destroy(stkde_ctx* c) {
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_ctr) cudaFree(c->d_ctr);
     if (c->d_count) cudaFree(c->d_count);
+    if (c->d_range) cudaFree(c->d_range);
     for (int i = 0; i <= MAX_PHASES; ++i)
         if (c->events_ok) cudaEventDestroy(c->ev[i]);
     delete c;
@@ -368,6 +417,99 @@ stkde_status stkde_compute(stkde_ctx* c, const double* points, int64_t n, const 
     }
     if (okind == 0) {
         cudaError_t e = cudaMemcpyAsync(out, dout, grid_bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+// Per-event bandwidths: the range of both arrays is read first (on the host, or
+// by a reduction kernel and one wait for the stream), the plan takes the largest
+// pair, the arrays are converted to voxel records next to the re-centred events
+// and gathered into bin order with them; the tile kernels weight each event by
+// (hs_max/hs_i)^2 (ht_max/ht_i).
+stkde_status stkde_compute_adaptive(stkde_ctx* c, const double* points, int64_t n,
+                                    const stkde_grid* g, const double* hs, const double* ht,
+                                    float* out) {
+    if (!c || !out || !g) return STKDE_ERR_INVALID_ARGUMENT;
+    if (n > 0 && (!hs || !ht)) return STKDE_ERR_INVALID_ARGUMENT;
+    // grid and event checks (the bandwidths are checked below)
+    stkde_status s = check_problem(points, n, g, g->sres, g->tres);
+    if (s != STKDE_OK) return s;
+    if (c->opt.form == STKDE_FORM_SCATTER) return STKDE_ERR_UNSUPPORTED;
+    if (n == 0) return stkde_compute(c, points, 0, g, g->sres, g->tres, out);
+    if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
+    const int okind = pointer_kind(out, c->device);
+    const int pkind = pointer_kind(points, c->device);
+    const int hkind = pointer_kind(hs, c->device), tkind = pointer_kind(ht, c->device);
+    if (okind < 0 || pkind < 0 || hkind < 0 || tkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
+
+    double lo[2], hi[2];
+    s = bandwidth_range(c, n, hs, ht, hkind, tkind, lo, hi);
+    if (s != STKDE_OK) return s;
+    s = check_problem(points, n, g, hi[0], hi[1]);
+    if (s != STKDE_OK) return s;
+    if (c->opt.form == STKDE_FORM_TENSOR_FP16X3) {
+        const double r = hi[0] / lo[0];
+        if (r * r * (hi[1] / lo[1]) > 16384.0) return STKDE_ERR_UNSUPPORTED;
+    }
+
+    const size_t grid_bytes = sizeof(float) * (size_t)g->gx * (size_t)g->gy * (size_t)g->gt;
+    float* dout = out;
+    if (okind == 0) {
+        if (grid_bytes > c->out_tmp_bytes) {
+            cudaStreamSynchronize(c->stream);
+            if (c->out_tmp) cudaFree(c->out_tmp);
+            c->out_tmp = nullptr; c->out_tmp_bytes = 0;
+            if (cudaMalloc(&c->out_tmp, grid_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return STKDE_ERR_OOM;
+            }
+            c->out_tmp_bytes = grid_bytes;
+        }
+        dout = c->out_tmp;
+    }
+    const Plan pl = make_plan(c->opt.kernel_constants, n, g, hi[0], hi[1], c->opt.slab);
+    const bool tensor = c->opt.form != STKDE_FORM_FP32;
+    const size_t order_bytes = tensor ? tile_order_bytes(pl) : 0;
+    const size_t nn = (size_t)n;
+    // the problem's workspace, then staging for host bandwidths and the two
+    // bandwidth record arrays
+    const size_t base = carve(nullptr, (int)n, pl.nkeys, pkind == 0, order_bytes, nullptr);
+    const size_t o_hs = base, o_ht = align_up(o_hs + (hkind == 0 ? 8 * nn : 0), 256);
+    const size_t o_evp = align_up(o_ht + (tkind == 0 ? 8 * nn : 0), 256);
+    const size_t o_evps = align_up(o_evp + 16 * nn, 256);
+    s = ensure_ws(c, align_up(o_evps + 16 * nn, 256));
+    if (s != STKDE_OK) return s;
+    Workspace w;
+    carve(c->ws, (int)n, pl.nkeys, pkind == 0, order_bytes, &w);
+    char* wb = static_cast<char*>(c->ws);
+    const double* dhs = hs;
+    const double* dht = ht;
+    cudaError_t e = cudaSuccess;
+    c->nphase = 0;
+    c->launches = 0;
+    if (hkind == 0) {
+        e = cudaMemcpyAsync(wb + o_hs, hs, 8 * nn, cudaMemcpyHostToDevice, c->stream);
+        dhs = reinterpret_cast<const double*>(wb + o_hs);
+    }
+    if (e == cudaSuccess && tkind == 0) {
+        e = cudaMemcpyAsync(wb + o_ht, ht, 8 * nn, cudaMemcpyHostToDevice, c->stream);
+        dht = reinterpret_cast<const double*>(wb + o_ht);
+    }
+    const double* dpts = points;
+    if (e == cudaSuccess && pkind == 0) {
+        e = cudaMemcpyAsync(w.pts, points, 24 * nn, cudaMemcpyHostToDevice, c->stream);
+        dpts = w.pts;
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    float4* evp = reinterpret_cast<float4*>(wb + o_evp);
+    float4* evps = reinterpret_cast<float4*>(wb + o_evps);
+    launch_bandwidths(dhs, dht, (int)n, g->sres, g->tres, evp, c->stream);
+    s = enqueue(c, dpts, pl, g, w, dout, evp, evps);
+    c->launches += 1 + (hkind == 1) + (tkind == 1);
+    if (s != STKDE_OK) return s;
+    if (okind == 0) {
+        e = cudaMemcpyAsync(out, dout, grid_bytes, cudaMemcpyDeviceToHost, c->stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
     return cuda_status(cudaGetLastError());
@@ -515,6 +657,48 @@ stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int c
     return cuda_status(cudaGetLastError());
 }
 
+// Update count of one problem; hs_i/ht_i: per-event bandwidths (device memory,
+// domain units) or NULL for the fixed pair hs, ht.  Host arrays are staged first.
+static stkde_status count_updates(stkde_ctx* c, const double* points, int64_t n,
+                                  const stkde_grid* g, double hs, double ht, const double* hs_i,
+                                  const double* ht_i, int hkind, int tkind, uint64_t* count) {
+    const int pkind = pointer_kind(points, c->device);
+    if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
+    const Plan pl = make_plan(c->opt.kernel_constants, n, g, hs, ht, c->opt.slab);
+    Workspace w;
+    const size_t nn = (size_t)n;
+    const size_t base = carve(nullptr, (int)n, pl.nkeys, pkind == 0, 0, nullptr);
+    const size_t o_hs = base, o_ht = align_up(o_hs + (hs_i && hkind == 0 ? 8 * nn : 0), 256);
+    stkde_status s = ensure_ws(c, align_up(o_ht + (ht_i && tkind == 0 ? 8 * nn : 0), 256));
+    if (s != STKDE_OK) return s;
+    carve(c->ws, (int)n, pl.nkeys, pkind == 0, 0, &w);
+    char* wb = static_cast<char*>(c->ws);
+    const double* dpts = points;
+    if (pkind == 0) {
+        cudaMemcpyAsync(w.pts, points, 24 * nn, cudaMemcpyHostToDevice, c->stream);
+        dpts = w.pts;
+    }
+    if (hs_i && hkind == 0) {
+        cudaMemcpyAsync(wb + o_hs, hs_i, 8 * nn, cudaMemcpyHostToDevice, c->stream);
+        hs_i = reinterpret_cast<const double*>(wb + o_hs);
+    }
+    if (ht_i && tkind == 0) {
+        cudaMemcpyAsync(wb + o_ht, ht_i, 8 * nn, cudaMemcpyHostToDevice, c->stream);
+        ht_i = reinterpret_cast<const double*>(wb + o_ht);
+    }
+    launch_recentre(dpts, (int)n, g->x0, g->y0, g->t0, g->sres, g->tres, pl, w.ev, w.keys, w.idx,
+                    c->d_err, c->stream);
+    cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream);
+    launch_count_updates(w.ev, (int)n, pl, hs / g->sres, ht / g->tres, hs_i, ht_i, g->sres, g->tres,
+                         c->d_count, c->stream);
+    unsigned long long h = 0;
+    cudaMemcpyAsync(&h, c->d_count, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    *count = h;
+    return STKDE_OK;
+}
+
 stkde_status stkde_count_updates(stkde_ctx* c, const double* points, int64_t n,
                                  const stkde_grid* g, double hs, double ht, uint64_t* count) {
     if (!c || !count) return STKDE_ERR_INVALID_ARGUMENT;
@@ -523,28 +707,27 @@ stkde_status stkde_count_updates(stkde_ctx* c, const double* points, int64_t n,
     *count = 0;
     if (n == 0) return STKDE_OK;
     if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
-    const int pkind = pointer_kind(points, c->device);
-    if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
-    const Plan pl = make_plan(c->opt.kernel_constants, n, g, hs, ht, c->opt.slab);
-    Workspace w;
-    s = ensure_ws(c, carve(nullptr, (int)n, pl.nkeys, pkind == 0, 0, nullptr));
+    return count_updates(c, points, n, g, hs, ht, nullptr, nullptr, 0, 0, count);
+}
+
+stkde_status stkde_count_updates_adaptive(stkde_ctx* c, const double* points, int64_t n,
+                                          const stkde_grid* g, const double* hs, const double* ht,
+                                          uint64_t* count) {
+    if (!c || !count || !g) return STKDE_ERR_INVALID_ARGUMENT;
+    if (n > 0 && (!hs || !ht)) return STKDE_ERR_INVALID_ARGUMENT;
+    stkde_status s = check_problem(points, n, g, g->sres, g->tres);
     if (s != STKDE_OK) return s;
-    carve(c->ws, (int)n, pl.nkeys, pkind == 0, 0, &w);
-    const double* dpts = points;
-    if (pkind == 0) {
-        cudaMemcpyAsync(w.pts, points, 24 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
-        dpts = w.pts;
-    }
-    launch_recentre(dpts, (int)n, g->x0, g->y0, g->t0, g->sres, g->tres, pl, w.ev, w.keys, w.idx,
-                    c->d_err, c->stream);
-    cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream);
-    launch_count_updates(w.ev, (int)n, pl, hs / g->sres, ht / g->tres, c->d_count, c->stream);
-    unsigned long long h = 0;
-    cudaMemcpyAsync(&h, c->d_count, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return cuda_status(e);
-    *count = h;
-    return STKDE_OK;
+    *count = 0;
+    if (n == 0) return STKDE_OK;
+    if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
+    const int hkind = pointer_kind(hs, c->device), tkind = pointer_kind(ht, c->device);
+    if (hkind < 0 || tkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
+    double lo[2], hi[2];
+    s = bandwidth_range(c, n, hs, ht, hkind, tkind, lo, hi);
+    if (s != STKDE_OK) return s;
+    s = check_problem(points, n, g, hi[0], hi[1]);
+    if (s != STKDE_OK) return s;
+    return count_updates(c, points, n, g, hi[0], hi[1], hs, ht, hkind, tkind, count);
 }
 
 int stkde_last_launch_count(stkde_ctx* c) { return c ? c->launches : 0; }

@@ -33,16 +33,22 @@ __device__ __forceinline__ TileGeom tile_geom(const Plan& pl, int tx, int ty, in
     return g;
 }
 
-// Does the event's cylinder reach a voxel centre of the tile?  A superset test
-// (bandwidths widened by 0.01 voxel): events that pass but reach nothing add zeros.
-__device__ __forceinline__ bool reaches(const Plan& pl, const TileGeom& g, float4 e) {
+// Does the cylinder of radius hsv and half-height htv (voxels) around the event
+// reach a voxel centre of the tile?  A superset test (bandwidths widened by 0.01
+// voxel): events that pass but reach nothing add zeros.
+__device__ __forceinline__ bool reaches_bw(const TileGeom& g, float4 e, float hsv, float htv) {
     const float dx = fmaxf(fmaxf(g.rx0 - e.x, e.x - g.rx1), 0.0f);
     const float dy = fmaxf(fmaxf(g.ry0 - e.y, e.y - g.ry1), 0.0f);
-    const float r = pl.hsv + 0.01f;
+    const float r = hsv + 0.01f;
     const bool xy = dx * dx + dy * dy < r * r;
-    const bool t = (e.z + pl.htv + 0.01f > (float)g.T0 + 0.5f) &&
-                   (e.z - pl.htv - 0.01f < (float)g.T1 - 0.5f);
+    const bool t = (e.z + htv + 0.01f > (float)g.T0 + 0.5f) &&
+                   (e.z - htv - 0.01f < (float)g.T1 - 0.5f);
     return xy && t;
+}
+
+// The same with the problem's bandwidths.
+__device__ __forceinline__ bool reaches(const Plan& pl, const TileGeom& g, float4 e) {
+    return reaches_bw(g, e, pl.hsv, pl.htv);
 }
 
 }  // namespace stkde

@@ -12,6 +12,11 @@
 // accumulators it holds in registers.  Each voxel is written once, zeros
 // included, so the grid needs no separate initialisation (the Theta(G) init of
 // Algorithm 2 becomes part of the store stream).
+//
+// With per-event bandwidths (ADAPT) each kept event also carries (hsv_i, htv_i,
+// 1/hsv_i, 1/htv_i): its reach test, T window and K_s, K_t use its own
+// bandwidths, and its K_t row is weighted by (hs_max/hs_i)^2 (ht_max/ht_i), the
+// plan holding the largest bandwidths and the matching normalisation.
 #include "internal.cuh"
 #include "tile_common.cuh"
 
@@ -25,10 +30,12 @@ constexpr int F_HALF = 32;       // T accumulators per thread
 constexpr int F_BATCH = 128;     // events per K_t table
 constexpr int F_BUF = F_BATCH + F_THREADS;
 
+template <bool ADAPT>
 __global__ void __launch_bounds__(F_THREADS, 2)
-k_tile_fp32(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__ start,
-            float* __restrict__ out) {
+k_tile_fp32(Plan pl, const float4* __restrict__ ev, const float4* __restrict__ evp,
+            const uint32_t* __restrict__ start, float* __restrict__ out) {
     __shared__ float4 buf[F_BUF];
+    __shared__ float4 bufp[ADAPT ? F_BUF : 1];  // per-event bandwidths of buf
     __shared__ __align__(16) float ktab[F_BATCH][F_TB];
     __shared__ int2 win[F_BATCH];
     __shared__ int wcount[F_THREADS / 32];
@@ -57,19 +64,28 @@ k_tile_fp32(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__
         // temporal invariants K_t[T] over the tile's T block (Algorithm 3's bar)
         for (int q = tid; q < cnt * F_TB; q += F_THREADS) {
             const int j = q / F_TB, c = q % F_TB;
-            const float w = ((float)(g.T0 + c) + 0.5f - buf[off + j].z) * pl.inv_ht;
-            ktab[j][c] = pl.ct * fmaxf(fmaf(-w, w, 1.0f), 0.0f);
+            if constexpr (ADAPT) {
+                const float4 b = bufp[off + j];
+                const float hr = pl.hsv * b.z;
+                const float w = ((float)(g.T0 + c) + 0.5f - buf[off + j].z) * b.w;
+                ktab[j][c] = (pl.ct * (hr * hr * (pl.htv * b.w))) * fmaxf(fmaf(-w, w, 1.0f), 0.0f);
+            } else {
+                const float w = ((float)(g.T0 + c) + 0.5f - buf[off + j].z) * pl.inv_ht;
+                ktab[j][c] = pl.ct * fmaxf(fmaf(-w, w, 1.0f), 0.0f);
+            }
         }
         for (int j = tid; j < cnt; j += F_THREADS) {
             const float pt = buf[off + j].z;
-            win[j] = make_int2((int)floorf(pt - 0.5f - pl.htv) - g.T0 - 1,
-                               (int)ceilf(pt - 0.5f + pl.htv) - g.T0 + 1);
+            const float htv = ADAPT ? bufp[off + j].y : pl.htv;
+            win[j] = make_int2((int)floorf(pt - 0.5f - htv) - g.T0 - 1,
+                               (int)ceilf(pt - 0.5f + htv) - g.T0 + 1);
         }
         __syncthreads();
         for (int j = 0; j < cnt; ++j) {
             const float4 e = buf[off + j];
-            const float u = (xc - e.x) * pl.inv_hs;
-            const float v = (yc - e.y) * pl.inv_hs;
+            const float ihs = ADAPT ? bufp[off + j].z : pl.inv_hs;
+            const float u = (xc - e.x) * ihs;
+            const float v = (yc - e.y) * ihs;
             const float s = fmaf(u, u, v * v);
             const float a = s < 1.0f ? pl.cs * fmaf(-u, u, 1.0f) * fmaf(-v, v, 1.0f) : 0.0f;
             if (!__any_sync(0xffffffffu, a != 0.0f)) continue;
@@ -101,11 +117,16 @@ k_tile_fp32(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__
             const int b = (int)start[kb + g.cy_hi + 1];
             for (int base = a; base < b; base += F_THREADS) {
                 const int p = base + tid;
-                float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 e = make_float4(0.f, 0.f, 0.f, 0.f), bw = e;
                 bool keep = false;
                 if (p < b) {
                     e = ev[p];
-                    keep = reaches(pl, g, e);
+                    if constexpr (ADAPT) {
+                        bw = evp[p];
+                        keep = reaches_bw(g, e, bw.x, bw.y);
+                    } else {
+                        keep = reaches(pl, g, e);
+                    }
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, keep);
                 if (lane == 0) wcount[warp] = __popc(bal);
@@ -117,7 +138,10 @@ k_tile_fp32(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__
                     pre += w < warp ? c : 0;
                     tot += c;
                 }
-                if (keep) buf[pre + __popc(bal & lt)] = e;
+                if (keep) {
+                    buf[pre + __popc(bal & lt)] = e;
+                    if constexpr (ADAPT) bufp[pre + __popc(bal & lt)] = bw;
+                }
                 const int cnt = s_count + tot;
                 __syncthreads();
                 if (tid == 0) s_count = cnt;
@@ -125,7 +149,10 @@ k_tile_fp32(Plan pl, const float4* __restrict__ ev, const uint32_t* __restrict__
                     const int full = (cnt / F_BATCH) * F_BATCH;
                     for (int off = 0; off < full; off += F_BATCH) process(off, F_BATCH);
                     const int rem = cnt - full;  // < F_BATCH <= full: no overlap
-                    for (int q = tid; q < rem; q += F_THREADS) buf[q] = buf[full + q];
+                    for (int q = tid; q < rem; q += F_THREADS) {
+                        buf[q] = buf[full + q];
+                        if constexpr (ADAPT) bufp[q] = bufp[full + q];
+                    }
                     if (tid == 0) s_count = rem;
                 }
                 __syncthreads();
@@ -162,7 +189,10 @@ void launch_tile_fp32(const Plan& pl, const Bins& b, float* out, int* err, cudaS
     p.ntb = (pl.gt + F_TB - 1) / F_TB;
     const int64_t items = (int64_t)p.ntx * p.nty * p.ntb;
     if (items <= 0) return;
-    k_tile_fp32<<<(unsigned)items, F_THREADS, 0, st>>>(p, b.ev, b.start, out);
+    if (b.evp)
+        k_tile_fp32<true><<<(unsigned)items, F_THREADS, 0, st>>>(p, b.ev, b.evp, b.start, out);
+    else
+        k_tile_fp32<false><<<(unsigned)items, F_THREADS, 0, st>>>(p, b.ev, nullptr, b.start, out);
 }
 
 }  // namespace stkde

@@ -52,6 +52,14 @@
 // earlier entries, and the streams share only the epilogue, which never waits on
 // a stream's producers, so no wait can close a cycle.
 //
+// With per-event bandwidths (ADAPT) a page holds 128 events followed by their
+// (hsv_i, htv_i, 1/hsv_i, 1/htv_i) records, both staged by the loader; the
+// filter and the column windows use each event's own bandwidths, the factor
+// tables its own 1/hsv_i (A) and 1/htv_i (B), and A carries the event's weight
+// (hs_max/hs_i)^2 (ht_max/ht_i) (the plan holds the largest bandwidths and the
+// normalisation 1/(n hs_max^2 ht_max)).  The weight scales both the product and
+// the disk-test difference of A, so the mask is unchanged.
+//
 // Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
 // kernel sets the timeout bit of the error word, every role leaves its loop,
 // outstanding copies and MMAs are drained with a second bounded wait, and the
@@ -73,7 +81,8 @@ constexpr int NGEN = 4;            // generator warps per stream
 constexpr int NEPI = 4;            // epilogue warps
 constexpr int WARP_EPI0 = 12;
 constexpr int NTHREADS = 16 * 32;
-constexpr int PAGE = 256;          // events per staging page
+constexpr int PAGE = 256;          // events per staging page (128 with per-event bandwidths)
+constexpr uint32_t PAGE_BYTES = PAGE * 16;
 constexpr int NPAGES = 5;          // pages per stream
 constexpr int CHUNK = 16;          // events per MMA (K of kind::f16)
 constexpr int MAXCH = PAGE / CHUNK;
@@ -275,7 +284,7 @@ __device__ __forceinline__ ProblemDev fetch_problem(const ProblemDev& single,
     return table ? table[p] : single;
 }
 
-template <bool FP16>
+template <bool FP16, bool ADAPT>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
           int* __restrict__ err, int* __restrict__ tile_ctr, const uint32_t* __restrict__ order,
@@ -318,6 +327,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
     ptx::tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(smem + L::OFF_MISC);
     const int gid = gen_id(warp);
+    constexpr int PEV = ADAPT ? PAGE / 2 : PAGE;  // events per page
 
     if (load_stream(warp) >= 0) {
         // ------------------------------------------------------------ loader
@@ -339,7 +349,8 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
         const uint32_t lt = (1u << lane) - 1u;
         auto filter_page = [&](uint32_t fq) {
             const uint32_t fp = p * NPAGES + fq % NPAGES;
-            float4* fb = reinterpret_cast<float4*>(smem + L::OFF_PAGES + fp * PAGE * 16);
+            float4* fb = reinterpret_cast<float4*>(smem + L::OFF_PAGES + fp * PAGE_BYTES);
+            float4* fbp = fb + PEV;  // per-event bandwidths (ADAPT)
             int2* ct = ctab + fp * MAXCH;
             uint16_t* ent = pent + fp * MAXENT;
             const int4 fm = pmeta[3 * fp], fmt4 = pmeta[3 * fp + 1];
@@ -348,15 +359,22 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 const Plan pl = fetch_problem(single, table, fmt4.w).pl;
                 const TileGeom fg = tile_geom(pl, fmt4.x, fmt4.y, fmt4.z, NB);
                 const int nev = fm.x, T0 = fg.T0, nbv = fg.T1 - fg.T0;
-                constexpr int R = PAGE / 32;
-                float4 e[R];
+                constexpr int R = PEV / 32;
+                float4 e[R], bw[R];
                 uint32_t bal[R];
 #pragma unroll
-                for (int r = 0; r < R; ++r) e[r] = fb[r * 32 + lane];
+                for (int r = 0; r < R; ++r) {
+                    e[r] = fb[r * 32 + lane];
+                    if constexpr (ADAPT) bw[r] = fbp[r * 32 + lane];
+                }
                 if (lane < MAXCH) ct[lane] = make_int2(0x7fffffff, -1);
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    bal[r] = __ballot_sync(0xffffffffu, r * 32 + lane < nev && reaches(pl, fg, e[r]));
+                for (int r = 0; r < R; ++r) {
+                    bool in = r * 32 + lane < nev;
+                    if constexpr (ADAPT) in = in && reaches_bw(fg, e[r], bw[r].x, bw[r].y);
+                    else in = in && reaches(pl, fg, e[r]);
+                    bal[r] = __ballot_sync(0xffffffffu, in);
+                }
                 __syncwarp();  // every read of the page before the first compacting write
                 // columns covered by each chunk's windows, clipped into the block
                 // (the filter's margin can keep an event whose window misses the
@@ -366,9 +384,11 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                     if ((bal[r] >> lane) & 1u) {
                         const uint32_t at = kept + __popc(bal[r] & lt);
                         fb[at] = e[r];
+                        if constexpr (ADAPT) fbp[at] = bw[r];
                         const float z = e[r].z;
-                        const int lo = min(max((int)ceilf(z - 0.5f - pl.htv) - T0, 0), nbv - 1);
-                        const int hi = min(max((int)floorf(z - 0.5f + pl.htv) - T0, lo), nbv - 1);
+                        const float htv = ADAPT ? bw[r].y : pl.htv;
+                        const int lo = min(max((int)ceilf(z - 0.5f - htv) - T0, 0), nbv - 1);
+                        const int hi = min(max((int)floorf(z - 0.5f + htv) - T0, lo), nbv - 1);
                         atomicMin(&ct[at / CHUNK].x, lo);
                         atomicMax(&ct[at / CHUNK].y, hi);
                     }
@@ -424,14 +444,16 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             return true;
         };
         // page meta: fill, flags, item, the item's tile coordinates and problem,
-        // and the problem's reciprocal bandwidths
-        auto close_page = [&](int flags, int64_t item, int tx, int ty, int tb, int pi, float ihs, float iht) {
+        // and the problem's reciprocal bandwidths and bandwidths
+        auto close_page = [&](int flags, int64_t item, int tx, int ty, int tb, int pi, const Plan* ppl) {
             __syncwarp();
             if (lane == 0) {
                 const uint32_t q = p * NPAGES + pg % NPAGES;
                 pmeta[3 * q] = make_int4((int)fill, flags, (int)(item & 0xffffffff), (int)(item >> 32));
                 pmeta[3 * q + 1] = make_int4(tx, ty, tb, pi);
-                pmeta[3 * q + 2] = make_int4(__float_as_int(ihs), __float_as_int(iht), 0, 0);
+                pmeta[3 * q + 2] = ppl ? make_int4(__float_as_int(ppl->inv_hs), __float_as_int(ppl->inv_ht),
+                                                   __float_as_int(ppl->hsv), __float_as_int(ppl->htv))
+                                       : make_int4(0, 0, 0, 0);
                 ptx::mbar_arrive(bar(L::pfull(p, pg % NPAGES)));
             }
             __syncwarp();
@@ -452,6 +474,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             const ProblemDev P = fetch_problem(single, table, pi);
             const Plan& pl = P.pl;
             const float4* __restrict__ ev = P.ev;
+            const float4* __restrict__ evp = P.evp;
             const uint32_t* __restrict__ start = P.start;
             const int64_t item = gk - P.item_base;  // tile of the problem
             int tx, ty, tb;
@@ -481,29 +504,32 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 while (done < tot) {
                     if (!open && !(ok = open_page())) break;
                     const uint32_t q = p * NPAGES + pg % NPAGES;
-                    const uint32_t take = min((uint32_t)PAGE - fill, tot - done);
+                    const uint32_t take = min((uint32_t)PEV - fill, tot - done);
                     // this page takes pass positions [done, done + take); each lane copies
                     // the part of its own run that falls there
                     const uint32_t lo = max(off, done), hi = min(off + len, done + take);
                     if (hi > lo) {
-                        ptx::mbar_expect_tx(bar(L::pfull(p, pg % NPAGES)), (hi - lo) * 16u);
-                        ptx::bulk_g2s(sb + L::OFF_PAGES + (q * PAGE + fill + (lo - done)) * 16u,
-                                      ev + a + (lo - off), (hi - lo) * 16u, bar(L::pfull(p, pg % NPAGES)));
+                        const uint32_t fb = bar(L::pfull(p, pg % NPAGES));
+                        const uint32_t dst = sb + L::OFF_PAGES + q * PAGE_BYTES + (fill + (lo - done)) * 16u;
+                        ptx::mbar_expect_tx(fb, (hi - lo) * (ADAPT ? 32u : 16u));
+                        ptx::bulk_g2s(dst, ev + a + (lo - off), (hi - lo) * 16u, fb);
+                        if constexpr (ADAPT)
+                            ptx::bulk_g2s(dst + PEV * 16u, evp + a + (lo - off), (hi - lo) * 16u, fb);
                     }
                     fill += take;
                     done += take;
-                    if (fill == (uint32_t)PAGE) close_page(0, item, tx, ty, tb, pi, pl.inv_hs, pl.inv_ht);
+                    if (fill == (uint32_t)PEV) close_page(0, item, tx, ty, tb, pi, &pl);
                 }
             }
             if (!ok) break;
             if (!open && !(ok = open_page())) break;
-            close_page(P_ITEM_END, item, tx, ty, tb, pi, pl.inv_hs, pl.inv_ht);  // the tile's last page, possibly empty
+            close_page(P_ITEM_END, item, tx, ty, tb, pi, &pl);  // the tile's last page, possibly empty
         }
         // termination page (every generator of the stream reads every page)
         if (ok) ok = filter_upto(pg);
-        if (ok && (ok = open_page())) close_page(P_TERM, 0, 0, 0, 0, 0, 0.f, 0.f);
+        if (ok && (ok = open_page())) close_page(P_TERM, 0, 0, 0, 0, 0, nullptr);
         if (!ok) {
-            if (open) close_page(P_TERM, 0, 0, 0, 0, 0, 0.f, 0.f);
+            if (open) close_page(P_TERM, 0, 0, 0, 0, 0, nullptr);
             for (uint32_t q = (pg > NPAGES ? pg - NPAGES : 0); q < pg; ++q)
                 drain_bar(bar(L::pfull(p, q % NPAGES)), (q / NPAGES) & 1u);
         }
@@ -514,6 +540,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
         float* xa = reinterpret_cast<float*>(tab + TAB_XA);
         float* yb = reinterpret_cast<float*>(tab + TAB_YB);
         float* tkt = reinterpret_cast<float*>(tab + TAB_TK);
+        float* tih = tkt + CHUNK;  // per-event 1/htv_i (ADAPT)
         const uint32_t fmt = FP16 ? 0u : 1u;
         bool ok = true;
         uint32_t ebase = 0;  // the stream's entries before the current page
@@ -550,7 +577,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
         for (uint32_t q = 0; ok; ++q) {
             const uint32_t pq = p * NPAGES + q % NPAGES;
             const uint32_t ph = (q / NPAGES) & 1u;
-            const float4* page = reinterpret_cast<const float4*>(smem + L::OFF_PAGES + pq * PAGE * 16);
+            const float4* page = reinterpret_cast<const float4*>(smem + L::OFF_PAGES + pq * PAGE_BYTES);
             if (!(ok = wait_warp(c, bar(L::pfull(p, q % NPAGES)), ph))) break;
             const int4 meta = pmeta[3 * pq], mt = pmeta[3 * pq + 1], mr = pmeta[3 * pq + 2];
             if (meta.y & P_TERM) {
@@ -561,6 +588,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             const int64_t item = (int64_t)(uint32_t)meta.z | ((int64_t)meta.w << 32);
             const int pi = mt.w;
             const float inv_hs = __int_as_float(mr.x), inv_ht = __int_as_float(mr.y);
+            const float hs_max = __int_as_float(mr.z), ht_max = __int_as_float(mr.w);
             const int end = meta.y & P_ITEM_END;
             const int X0 = mt.x * TX, Y0 = mt.y * TY, T0 = mt.z * NB;
             if (!(ok = wait_warp(c, bar(L::pfilt(p, q % NPAGES)), ph))) break;
@@ -594,26 +622,42 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 const bool real = k < count;
                 float4 ek = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (real) ek = page[ch * CHUNK + k];
-                const float cu = real ? ((float)X0 + 0.5f - ek.x) * inv_hs : 2.0f;
-                const float cv = real ? ((float)Y0 + 0.5f - ek.y) * inv_hs : 2.0f;
+                // the event's bandwidth reciprocals and weight (ADAPT), else the plan's
+                float ihs = inv_hs, iht = inv_ht, wk = 1.0f;
+                if constexpr (ADAPT) {
+                    if (real) {
+                        const float4 bk = page[PEV + ch * CHUNK + k];
+                        ihs = bk.z;
+                        iht = bk.w;
+                        const float hr = hs_max * bk.z;
+                        wk = hr * hr * (ht_max * bk.w);
+                    }
+                }
+                const float cu = real ? ((float)X0 + 0.5f - ek.x) * ihs : 2.0f;
+                const float cv = real ? ((float)Y0 + 0.5f - ek.y) * ihs : 2.0f;
 #pragma unroll
                 for (int i = 0; i < TX / 2; ++i) {
                     const int x = half + 2 * i;
-                    const float u = fmaf((float)x, inv_hs, cu);
-                    xa[x * XA_STRIDE + k] = fmaf(-u, u, 1.0f);
+                    const float u = fmaf((float)x, ihs, cu);
+                    if constexpr (ADAPT) xa[x * XA_STRIDE + k] = wk * fmaf(-u, u, 1.0f);
+                    else xa[x * XA_STRIDE + k] = fmaf(-u, u, 1.0f);
                 }
 #pragma unroll
                 for (int i = 0; i < TY / 2; ++i) {
                     const int y = half + 2 * i;
-                    const float v = fmaf((float)y, inv_hs, cv);
+                    const float v = fmaf((float)y, ihs, cv);
                     const float vv = v * v;
                     yb[y * YB_STRIDE + k] = 1.0f - vv;
-                    yb[y * YB_STRIDE + 16 + k] = vv;
+                    if constexpr (ADAPT) yb[y * YB_STRIDE + 16 + k] = wk * vv;
+                    else yb[y * YB_STRIDE + 16 + k] = vv;
                 }
                 const int cw = c0 + w * NCAP;
                 const int ncols = min(NCAP, cend - cw);
                 // event time relative to the window's first voxel centre
-                if (lane < CHUNK) tkt[lane] = real ? ek.z - ((float)(T0 + cw) + 0.5f) : 1.0e9f;
+                if (lane < CHUNK) {
+                    tkt[lane] = real ? ek.z - ((float)(T0 + cw) + 0.5f) : 1.0e9f;
+                    if constexpr (ADAPT) tih[lane] = iht;
+                }
                 __syncwarp();
                 if (!(ok = slot_wait(e))) break;
                 uint8_t* st = smem + L::OFF_STAGE + (p * NSTAGE + e % NSTAGE) * STAGE_BYTES;
@@ -663,12 +707,17 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 }
                 // B = K_t without c_t: (1 - w^2)_+ for the window's columns
                 {
-                    float2 tq[8];
+                    float2 tq[8], iq[8];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const float4 t4 = *reinterpret_cast<const float4*>(tkt + 4 * i);
                         tq[2 * i] = make_float2(-t4.x, -t4.y);
                         tq[2 * i + 1] = make_float2(-t4.z, -t4.w);
+                        if constexpr (ADAPT) {
+                            const float4 i4 = *reinterpret_cast<const float4*>(tih + 4 * i);
+                            iq[2 * i] = make_float2(i4.x, i4.y);
+                            iq[2 * i + 1] = make_float2(i4.z, i4.w);
+                        }
                     }
                     const float2 ih2 = make_float2(inv_ht, inv_ht), one2 = make_float2(1.0f, 1.0f);
                     uint8_t* bh = st + 2 * A_BYTES;
@@ -678,7 +727,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                         uint32_t h[8], l[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            const float2 wv = __fmul2_rn(__fadd2_rn(n2, tq[i]), ih2);
+                            const float2 wv = __fmul2_rn(__fadd2_rn(n2, tq[i]), ADAPT ? iq[i] : ih2);
                             const float2 kt = __ffma2_rn(fneg2(wv), wv, one2);
                             split_rn<FP16>(make_float2(fmaxf(kt.x, 0.0f), fmaxf(kt.y, 0.0f)), h[i], l[i]);
                         }
@@ -929,10 +978,10 @@ __global__ void k_tile_order(int nitems, const uint32_t* __restrict__ cost,
     order[base + atomicAdd(&cursor[b], 1u)] = (uint32_t)i;
 }
 
-template <bool FP16>
+template <bool FP16, bool ADAPT>
 bool launch_cfg(const ProblemDev& single, const ProblemDev* table, int nprob, int64_t items,
                 int* err, int* tile_ctr, uint32_t* order_ws, cudaStream_t st) {
-    auto kern = k_tile_tc<FP16>;
+    auto kern = k_tile_tc<FP16, ADAPT>;
     static bool attr = false;
     if (!attr) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::TOTAL) !=
@@ -988,17 +1037,21 @@ bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* ti
     single.start = b.start;
     single.out = out;
     single.item_base = 0;
+    single.evp = b.evp;
     const int64_t items = tile_tc_items(pl);
-    return fp16 ? launch_cfg<true>(single, nullptr, 1, items, err, tile_ctr, order_ws, st)
-                : launch_cfg<false>(single, nullptr, 1, items, err, tile_ctr, order_ws, st);
+    if (b.evp)
+        return fp16 ? launch_cfg<true, true>(single, nullptr, 1, items, err, tile_ctr, order_ws, st)
+                    : launch_cfg<false, true>(single, nullptr, 1, items, err, tile_ctr, order_ws, st);
+    return fp16 ? launch_cfg<true, false>(single, nullptr, 1, items, err, tile_ctr, order_ws, st)
+                : launch_cfg<false, false>(single, nullptr, 1, items, err, tile_ctr, order_ws, st);
 }
 
 bool launch_tile_tc_batch(const ProblemDev* table, int nprob, int64_t total_items, int* err,
                           int* tile_ctr, uint32_t* order_ws, int fp16, cudaStream_t st) {
     if (nprob <= 0) return true;
     const ProblemDev none{};
-    return fp16 ? launch_cfg<true>(none, table, nprob, total_items, err, tile_ctr, order_ws, st)
-                : launch_cfg<false>(none, table, nprob, total_items, err, tile_ctr, order_ws, st);
+    return fp16 ? launch_cfg<true, false>(none, table, nprob, total_items, err, tile_ctr, order_ws, st)
+                : launch_cfg<false, false>(none, table, nprob, total_items, err, tile_ctr, order_ws, st);
 }
 
 }  // namespace stkde

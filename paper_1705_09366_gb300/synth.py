@@ -137,6 +137,19 @@ def resident_sets(seed_offset: int = 0, sizes=(50_000, 200_000, 1_000_000, 2_000
             for n in sizes]
 
 
+def adaptive_bandwidths(n: int, hs: float, ht: float, spread: float = 2.0,
+                        seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Per-event bandwidths (domain units) log-uniform in [h / spread, h * spread]
+    around the fixed pair (hs, ht), drawn independently per event and axis: a
+    stand-in for bandwidths adapted to the local population density, which the
+    caller would derive from data this module does not have."""
+    rng = _rng(SEED_BASE + 5 + 7 * seed)
+    ls = math.log(spread)
+    hsi = hs * np.exp(rng.uniform(-ls, ls, n))
+    hti = ht * np.exp(rng.uniform(-ls, ls, n))
+    return np.ascontiguousarray(hsi), np.ascontiguousarray(hti)
+
+
 def tiny(rng: np.random.Generator, n: int, gx: int, gy: int, gt: int, spill: float = 0.25) -> np.ndarray:
     """Uniform events over the grid widened by ``spill`` of each side, so some
     fall outside it (for brute-force comparisons on tiny inputs)."""

@@ -157,3 +157,19 @@ def test_empty_input_is_zero():
     z = np.zeros((0, 3))
     assert not oracle.pb_adaptive(z, np.zeros(0), np.zeros(0), p).any()
     assert not oracle.vb_adaptive(z, np.zeros(0), np.zeros(0), p).any()
+
+
+def test_box_pair_counts_equal_per_event_update_counts():
+    """The in-cylinder pairs the adaptive boxes count add up to the sum of the
+    fixed-bandwidth update counts of each event with its own bandwidths."""
+    rng = np.random.default_rng(31)
+    n = 30
+    dims, org, res, pts, hs, ht = _random_problem(rng, n)
+    kw = dict(x0=org[0], y0=org[1], t0=org[2], sres=res[0], tres=res[1])
+    p = oracle.params(*dims, 1.0, 1.0, **kw)
+    gx, gy, gt = dims
+    boxes = [(0, gx // 2, 0, gy, 0, gt), (gx // 2, gx, 0, gy, 0, gt)]
+    _, counts = oracle.pb_adaptive_boxes(pts, hs, ht, p, boxes, pair_counts=True)
+    ref = sum(oracle.count_updates(pts[i:i + 1], oracle.params(*dims, hs[i], ht[i], **kw))
+              for i in range(n))
+    assert int(counts.sum()) == ref
