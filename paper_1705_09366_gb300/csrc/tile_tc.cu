@@ -13,10 +13,12 @@
 // accumulated (the dropped lo*lo term is below 2^-15 relative).
 //
 // The tensor cores round each accumulation step toward zero, so a long run of
-// steps into one accumulator drifts low.  The MMA warp therefore closes an
-// accumulator "segment" before any 32-column block of it has taken more than a
-// fixed number of chunks; the epilogue stores the first segment of a tile and
-// adds later ones to it in fp32 (round to nearest), which bounds the drift.
+// steps into one accumulator drifts low.  The MMA warp therefore counts the
+// chunks each 32-column block of the accumulator has taken and, before a block
+// would reach a fixed count, hands just the blocks at the limit to the epilogue
+// (a "flush"): the first drain of a block stores it, later drains add to the
+// stored values in fp32 (round to nearest), which bounds the drift.  The tile's
+// last drain writes every block, zeros included, so each voxel is stored once.
 //
 // Persistent CTA per SM holding two independent pipelines ("streams"), each
 // with its own loader, four generators, stage ring, MMA warp and 256-column
@@ -45,9 +47,9 @@
 //                     shared memory layout.
 //   warps 12-15       epilogue: one per tensor-memory lane quarter; scales by
 //                     c_s c_t / (n hs^2 ht), writes each voxel of the tile
-//                     (vector stores), adds later segments, zeroes the
-//                     accumulator.  It serves whichever stream has a segment
-//                     ready.
+//                     (vector stores), adds later drains of a block, zeroes
+//                     the drained blocks.  It serves whichever stream has a
+//                     drain ready.
 // The builder of a stream's earliest unbuilt entry only waits on that stream's
 // earlier entries, and the streams share only the epilogue, which never waits on
 // a stream's producers, so no wait can close a cycle.
@@ -111,8 +113,11 @@ constexpr int F_TERM = 8;       // end of the stream's sequence
 // page meta flags (written by the loader)
 constexpr int P_ITEM_END = 4;
 constexpr int P_TERM = 8;
-// segment descriptor flags (MMA warp -> epilogue)
-constexpr int D_FIRST = 1, D_LAST = 2, D_TERM = 4;
+// drain descriptor flags (MMA warp -> epilogue); the descriptor's fourth word
+// holds the blocks touched since their last drain (bits 0-7), the blocks to
+// drain (bits 8-15, all of them with D_LAST) and the blocks already stored
+// (bits 16-23)
+constexpr int D_LAST = 2, D_TERM = 4;
 
 // roles
 __device__ __forceinline__ int mma_stream(int w) { return w == 0 ? 0 : w == 8 ? 1 : -1; }
@@ -707,14 +712,15 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 }
                 // B = K_t without c_t: (1 - w^2)_+ for the window's columns
                 {
-                    float2 tq[8], iq[8];
+                    const int hh = lane & 1;  // events 8 hh .. 8 hh + 7
+                    float2 tq[4], iq[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float4 t4 = *reinterpret_cast<const float4*>(tkt + 4 * i);
+                    for (int i = 0; i < 2; ++i) {
+                        const float4 t4 = *reinterpret_cast<const float4*>(tkt + 8 * hh + 4 * i);
                         tq[2 * i] = make_float2(-t4.x, -t4.y);
                         tq[2 * i + 1] = make_float2(-t4.z, -t4.w);
                         if constexpr (ADAPT) {
-                            const float4 i4 = *reinterpret_cast<const float4*>(tih + 4 * i);
+                            const float4 i4 = *reinterpret_cast<const float4*>(tih + 8 * hh + 4 * i);
                             iq[2 * i] = make_float2(i4.x, i4.y);
                             iq[2 * i + 1] = make_float2(i4.z, i4.w);
                         }
@@ -722,20 +728,19 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                     const float2 ih2 = make_float2(inv_ht, inv_ht), one2 = make_float2(1.0f, 1.0f);
                     uint8_t* bh = st + 2 * A_BYTES;
                     uint8_t* bl = bh + B_BYTES;
-                    for (int n = lane; n < ncols; n += 32) {
+                    for (int it = lane; it < 2 * ncols; it += 32) {
+                        const int n = it >> 1;
                         const float2 n2 = make_float2((float)n, (float)n);
-                        uint32_t h[8], l[8];
+                        uint32_t h[4], l[4];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
+                        for (int i = 0; i < 4; ++i) {
                             const float2 wv = __fmul2_rn(__fadd2_rn(n2, tq[i]), ADAPT ? iq[i] : ih2);
                             const float2 kt = __ffma2_rn(fneg2(wv), wv, one2);
                             split_rn<FP16>(make_float2(fmaxf(kt.x, 0.0f), fmaxf(kt.y, 0.0f)), h[i], l[i]);
                         }
-                        const uint32_t off = (uint32_t)(n >> 3) * CORE_SBO + (uint32_t)(n & 7) * 16;
+                        const uint32_t off = (uint32_t)(n >> 3) * CORE_SBO + (uint32_t)(n & 7) * 16 + hh * CORE_LBO;
                         *reinterpret_cast<uint4*>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
-                        *reinterpret_cast<uint4*>(bh + off + CORE_LBO) = make_uint4(h[4], h[5], h[6], h[7]);
                         *reinterpret_cast<uint4*>(bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
-                        *reinterpret_cast<uint4*>(bl + off + CORE_LBO) = make_uint4(l[4], l[5], l[6], l[7]);
                     }
                 }
                 const int fl = F_MMA | ((end && ch == nch - 1 && w + 1 == nw) ? F_ITEM_END : 0);
@@ -753,26 +758,26 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
         // The whole warp runs the loop (converged); one elected lane issues.
         const int p = mma_stream(warp);
         const uint32_t acc = tmem + (uint32_t)(p * NB);
-        uint32_t nseg = 0;  // accumulator segments closed so far
+        uint32_t nseg = 0;  // drains handed to the epilogue so far
         bool ok = true;
         // descriptors of the stream's stage 0; stage s adds s * STAGE_BYTES / 16
         const uint64_t d_ahi = ptx::smem_desc(sb + L::OFF_STAGE + p * NSTAGE * STAGE_BYTES, CORE_LBO, CORE_SBO);
         const uint64_t d_alo = d_ahi + (A_BYTES >> 4);
         const uint64_t d_bhi = d_ahi + ((2 * A_BYTES) >> 4);
         const uint64_t d_blo = d_ahi + ((2 * A_BYTES + B_BYTES) >> 4);
-        // chunks per 32-column block at which a segment is closed (a power of
-        // two below 128), as a bit mask over the four byte counters of a word
+        // chunks per 32-column block at which the block is drained (a power of
+        // two, at most 128), as a bit mask over the four byte counters of a word
         const uint32_t flush4 = (uint32_t)flush_chunks * 0x01010101u;
         const int4* hdr = reinterpret_cast<const int4*>(smem + L::OFF_HDR + p * NSTAGE * 32);
         int4* desc = reinterpret_cast<int4*>(smem + L::OFF_DESC + p * 16);
-        int first = 1;
-        uint32_t touched = 0;             // 32-column blocks written in this segment
+        uint32_t stored = 0;              // 32-column blocks of the tile already in global memory
+        uint32_t touched = 0;             // 32-column blocks written since their last drain
         uint32_t cnt_lo = 0, cnt_hi = 0;  // chunks per 32-column block (bytes)
-        // hands the current segment to the epilogue and waits until it has been
-        // drained (this stream has one accumulator)
-        auto close_segment = [&](int tile, int pi, int flags) -> bool {
+        // hands the blocks `drain` (all blocks with D_LAST) to the epilogue and
+        // waits until they have been drained (this stream has one accumulator)
+        auto close_segment = [&](int tile, int pi, int flags, uint32_t drain) -> bool {
             if (lane == 0) {
-                *desc = make_int4(tile, pi, flags, (int)touched);
+                *desc = make_int4(tile, pi, flags, (int)(touched | (drain << 8) | (stored << 16)));
                 ptx::mbar_arrive(bar(L::dfull(p)));
             }
             __syncwarp();
@@ -781,9 +786,20 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             if (flags & D_TERM) return true;
             if (!wait_warp(c, bar(L::aempty(p)), nseg & 1u)) return false;
             ptx::tc_fence_after();
-            touched = 0;
-            cnt_lo = 0;
-            cnt_hi = 0;
+            if (flags & D_LAST) {
+                touched = 0;
+                stored = 0;
+                cnt_lo = 0;
+                cnt_hi = 0;
+            } else {
+                stored |= drain;
+                touched &= ~drain;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    if ((drain >> b) & 1u) cnt_lo &= ~(0xffu << (8 * b));
+                    if ((drain >> (4 + b)) & 1u) cnt_hi &= ~(0xffu << (8 * b));
+                }
+            }
             return true;
         };
         ok = wait_warp(c, bar(L::aempty(p)), 0);
@@ -795,7 +811,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             const int4 h0 = hdr[2 * s], h1 = hdr[2 * s + 1];
             const int flags = h0.z;
             if (flags & F_TERM) {
-                close_segment(0, 0, D_TERM);
+                close_segment(0, 0, D_TERM, 0);
                 break;
             }
             const int tile = h1.z, pi = h1.w;
@@ -811,11 +827,17 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 } else {
                     const uint32_t inc_lo = (uint32_t)h1.x, inc_hi = (uint32_t)h1.y;
                     // a byte (chunk count of one 32-column block) reaching the
-                    // power-of-two flush count closes the segment first
-                    if (((cnt_lo + inc_lo) | (cnt_hi + inc_hi)) & flush4) {
-                        // close the segment: the epilogue adds it in fp32
-                        if (!(ok = close_segment(tile, pi, first ? D_FIRST : 0))) break;
-                        first = 0;
+                    // power-of-two flush count drains that block first
+                    const uint32_t ov_lo = (cnt_lo + inc_lo) & flush4, ov_hi = (cnt_hi + inc_hi) & flush4;
+                    if (ov_lo | ov_hi) {
+                        // drain just the blocks that reached the flush count
+                        uint32_t drain = 0;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            if ((ov_lo >> (8 * b)) & 0xffu) drain |= 1u << b;
+                            if ((ov_hi >> (8 * b)) & 0xffu) drain |= 1u << (4 + b);
+                        }
+                        if (!(ok = close_segment(tile, pi, 0, drain))) break;
                     }
                     cnt_lo += inc_lo;
                     cnt_hi += inc_hi;
@@ -825,8 +847,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 }
             }
             if (flags & F_ITEM_END) {
-                if (!(ok = close_segment(tile, pi, (first ? D_FIRST : 0) | D_LAST))) break;
-                first = 1;
+                if (!(ok = close_segment(tile, pi, D_LAST, 0xffu))) break;
             }
             commit_elect(bar(L::sempty(p, s)));
         }
@@ -876,8 +897,9 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             const bool vec = (pl.gt & 3) == 0;
             // A and B carry neither c_s nor c_t: both join the normalisation here
             const float scale = pl.norm * (pl.cs * pl.ct);
-            const bool first = (dsc.z & D_FIRST) != 0, last = (dsc.z & D_LAST) != 0;
-            const uint32_t touched = (uint32_t)dsc.w;
+            const bool last = (dsc.z & D_LAST) != 0;
+            const uint32_t touched = (uint32_t)dsc.w & 0xffu, drain = ((uint32_t)dsc.w >> 8) & 0xffu;
+            const uint32_t stored = ((uint32_t)dsc.w >> 16) & 0xffu;
             int tx, ty, tb;
             decode_item(pl, item, tx, ty, tb);
             const int m = 32 * qtr + lane;
@@ -886,7 +908,10 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             const bool valid = X < pl.gx && Y < pl.gy;
             float* dst = out + ((int64_t)X * pl.gy + Y) * (int64_t)pl.gt + T0;
             for (int col = 0; col < nbv; col += 32) {
-                const bool hit = (touched >> (col >> 5)) & 1u;
+                const int bk = col >> 5;
+                const bool hit = (touched >> bk) & 1u;
+                const bool first = !((stored >> bk) & 1u);
+                if (!(last || ((drain >> bk) & 1u))) continue;
                 if (!first && !hit) continue;
                 uint32_t r[32];
                 const uint32_t ta = trow + (uint32_t)(p * NB + col);
@@ -898,7 +923,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 if (vec && nv == 32) {
                     float4* p4 = reinterpret_cast<float4*>(dst + col);
                     float4 pv[8];
-                    if (!first) {  // earlier segments of this tile: load all, then add
+                    if (!first) {  // earlier drains of this block: load all, then add
 #pragma unroll
                         for (int v4 = 0; v4 < 8; ++v4) pv[v4] = p4[v4];
                     }
@@ -1008,9 +1033,9 @@ bool launch_cfg(const ProblemDev& single, const ProblemDev* table, int nprob, in
         k_tile_order<<<blocks, 256, 0, st>>>((int)items, cost, hist, cursor, ord);
         order = ord;
     }
-    // chunks (three accumulation steps each) per 32-column block at which a
-    // segment is closed (a power of two: the MMA warp tests it as a bit mask):
-    // bounds the round-toward-zero drift of the tensor-core accumulation per segment
+    // chunks (three accumulation steps each) per 32-column block at which the
+    // block is drained (a power of two: the MMA warp tests it as a bit mask):
+    // bounds the round-toward-zero drift of the tensor-core accumulation per drain
     const int flush_chunks = FP16 ? 64 : 128;
     kern<<<grid, NTHREADS, L::TOTAL, st>>>(single, table, nprob, err, tile_ctr, order, items,
                                            flush_chunks);
