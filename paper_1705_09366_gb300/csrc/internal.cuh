@@ -52,6 +52,7 @@ struct ProblemDev {
     const uint32_t* start;    // the problem's bin boundaries start[0 .. nkeys]
     float* out;               // the problem's output grid, device memory
     const float4* evp;        // per-event bandwidths in sorted order (NULL: the plan's)
+    int tx0, ntxg;            // the launch's tiles cover tile columns tx0 .. tx0 + ntxg - 1 (ntxg 0: all)
 };
 
 // Per-problem device buffers (views into the context's workspace).
@@ -113,8 +114,10 @@ size_t tile_order_bytes_items(int64_t items);
 // here on the stream before the kernel).  order_ws: tile_order_bytes(pl) of device
 // scratch for the heaviest-first tile order (two extra launches), or NULL to take
 // the tiles in index order.
+// tx0, ntxg: only the tiles of tile columns tx0 .. tx0 + ntxg - 1 (ntxg 0: all), so
+// that a grid can be computed in slabs of X whose copies overlap later slabs.
 bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* tile_ctr,
-                    uint32_t* order_ws, int fp16, cudaStream_t st);
+                    uint32_t* order_ws, int fp16, cudaStream_t st, int tx0 = 0, int ntxg = 0);
 // The same over the tiles of all problems of a batch in one launch: `table` is
 // the batch's problem table in device memory (nprob entries, item_base set to
 // the running sum of tile_tc_items), total_items the sum; order_ws holds

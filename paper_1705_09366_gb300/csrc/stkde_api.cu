@@ -17,6 +17,11 @@ namespace {
 
 constexpr int MAX_PHASES = 5;
 constexpr uint32_t MAX_KEYS = 1u << 25;
+// Host outputs of the tensor forms: the tile kernel runs in up to MAX_SLABS slabs
+// of X, each at least SLAB_MIN_BYTES of output, and each slab's copy to the host
+// overlaps the later slabs' kernels.
+constexpr int MAX_SLABS = 8;
+constexpr size_t SLAB_MIN_BYTES = (size_t)64 << 20;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -38,6 +43,10 @@ struct stkde_ctx {
     cudaEvent_t ev[MAX_PHASES + 1];
     int nphase = 0;
     bool events_ok = false;
+    cudaStream_t copy_stream = nullptr;  // host-output copies of slabs
+    cudaEvent_t slab_ev[MAX_SLABS] = {};
+    cudaEvent_t copy_done = nullptr;
+    bool slabs_ok = false;
     int launches = 0;          // kernels enqueued by the last compute call
 };
 
@@ -166,10 +175,16 @@ void mark(stkde_ctx* c) {
 
 // Enqueues one problem whose events are already on the device.  The result goes
 // to the device buffer `out`.  With per-event bandwidths, evp holds their
-// records in input order and evp_sorted receives them in bin order.
+// records in input order and evp_sorted receives them in bin order.  With
+// host_out (a host buffer for the grid), a tensor-form grid of at least two slabs
+// is computed slab by slab along X and each slab is copied to host_out on the
+// context's copy stream while the next slabs compute; *copied tells the caller
+// that the copy is enqueued (the context's stream waits for it).
 stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stkde_grid* g,
                      const Workspace& w, float* out, const float4* evp = nullptr,
-                     float4* evp_sorted = nullptr) {
+                     float4* evp_sorted = nullptr, float* host_out = nullptr,
+                     bool* copied = nullptr) {
+    if (copied) *copied = false;
     cudaStream_t st = c->stream;
     const int form = c->opt.form;
     const int n = pl.n;
@@ -202,11 +217,46 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
     if (form == STKDE_FORM_FP32) {
         launch_tile_fp32(pl, b, out, c->d_err, st);
     } else {
-        // heaviest tiles first (two small launches), then the tile kernel
-        if (!launch_tile_tc(pl, b, out, c->d_err, c->d_ctr, w.order,
-                            form == STKDE_FORM_TENSOR_FP16X3 ? 1 : 0, st))
-            return STKDE_ERR_UNSUPPORTED;
-        c->launches += 2;
+        const int fp16 = form == STKDE_FORM_TENSOR_FP16X3 ? 1 : 0;
+        const size_t row_bytes = sizeof(float) * (size_t)pl.gy * (size_t)pl.gt;  // one X row
+        const size_t grid_bytes = row_bytes * (size_t)pl.gx;
+        int nslab = 1;
+        if (host_out && c->slabs_ok) {
+            nslab = (int)(grid_bytes / SLAB_MIN_BYTES);
+            nslab = nslab < MAX_SLABS ? nslab : MAX_SLABS;
+            nslab = nslab < pl.ntx ? nslab : pl.ntx;
+        }
+        if (nslab < 2) {
+            // heaviest tiles first (two small launches), then the tile kernel
+            if (!launch_tile_tc(pl, b, out, c->d_err, c->d_ctr, w.order, fp16, st))
+                return STKDE_ERR_UNSUPPORTED;
+            c->launches += 2;
+        } else {
+            // every kernel first, then every copy: a copy into pageable memory
+            // may hold the calling thread until it is done
+            int lo[MAX_SLABS + 1];
+            for (int k = 0; k <= nslab; ++k) lo[k] = (int)((int64_t)pl.ntx * k / nslab);
+            for (int k = 0; k < nslab; ++k) {
+                if (!launch_tile_tc(pl, b, out, c->d_err, c->d_ctr, w.order, fp16, st, lo[k],
+                                    lo[k + 1] - lo[k]))
+                    return STKDE_ERR_UNSUPPORTED;
+                cudaEventRecord(c->slab_ev[k], st);
+            }
+            c->launches += 3 * nslab - 1;
+            for (int k = 0; k < nslab; ++k) {
+                const size_t x0 = (size_t)lo[k] * TX;
+                const size_t x1 = (size_t)(lo[k + 1] * TX < pl.gx ? lo[k + 1] * TX : pl.gx);
+                cudaStreamWaitEvent(c->copy_stream, c->slab_ev[k], 0);
+                cudaError_t e = cudaMemcpyAsync(host_out + x0 * (row_bytes / sizeof(float)),
+                                                out + x0 * (row_bytes / sizeof(float)),
+                                                (x1 - x0) * row_bytes, cudaMemcpyDeviceToHost,
+                                                c->copy_stream);
+                if (e != cudaSuccess) return cuda_status(e);
+            }
+            cudaEventRecord(c->copy_done, c->copy_stream);
+            cudaStreamWaitEvent(st, c->copy_done, 0);
+            if (copied) *copied = true;
+        }
     }
     c->launches += 1;
     mark(c);
@@ -328,6 +378,11 @@ stkde_status stkde_create(stkde_ctx** out, const stkde_options* opt) {
     c->events_ok = true;
     for (int i = 0; i <= MAX_PHASES; ++i)
         if (cudaEventCreate(&c->ev[i]) != cudaSuccess) c->events_ok = false;
+    c->slabs_ok = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < MAX_SLABS && c->slabs_ok; ++i)
+        c->slabs_ok = cudaEventCreateWithFlags(&c->slab_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    cudaGetLastError();
     cudaDeviceSynchronize();
     *out = c;
     return STKDE_OK;
@@ -345,6 +400,13 @@ void stkde_destroy(stkde_ctx* c) {
     if (c->d_range) cudaFree(c->d_range);
     for (int i = 0; i <= MAX_PHASES; ++i)
         if (c->events_ok) cudaEventDestroy(c->ev[i]);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    if (c->copy_done) cudaEventDestroy(c->copy_done);
+    for (int i = 0; i < MAX_SLABS; ++i)
+        if (c->slab_ev[i]) cudaEventDestroy(c->slab_ev[i]);
     delete c;
 }
 
@@ -388,6 +450,7 @@ stkde_status stkde_compute(stkde_ctx* c, const double* points, int64_t n, const 
     }
     c->nphase = 0;
     c->launches = 0;
+    bool copied = false;
     if (n == 0) {
         cudaMemsetAsync(dout, 0, grid_bytes, c->stream);
     } else {
@@ -412,10 +475,10 @@ stkde_status stkde_compute(stkde_ctx* c, const double* points, int64_t n, const 
             if (e != cudaSuccess) return cuda_status(e);
             dpts = w.pts;
         }
-        s = enqueue(c, dpts, pl, g, w, dout);
+        s = enqueue(c, dpts, pl, g, w, dout, nullptr, nullptr, okind == 0 ? out : nullptr, &copied);
         if (s != STKDE_OK) return s;
     }
-    if (okind == 0) {
+    if (okind == 0 && !copied) {
         cudaError_t e = cudaMemcpyAsync(out, dout, grid_bytes, cudaMemcpyDeviceToHost, c->stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
@@ -505,10 +568,11 @@ stkde_status stkde_compute_adaptive(stkde_ctx* c, const double* points, int64_t 
     float4* evp = reinterpret_cast<float4*>(wb + o_evp);
     float4* evps = reinterpret_cast<float4*>(wb + o_evps);
     launch_bandwidths(dhs, dht, (int)n, g->sres, g->tres, evp, c->stream);
-    s = enqueue(c, dpts, pl, g, w, dout, evp, evps);
+    bool copied = false;
+    s = enqueue(c, dpts, pl, g, w, dout, evp, evps, okind == 0 ? out : nullptr, &copied);
     c->launches += 1 + (hkind == 1) + (tkind == 1);
     if (s != STKDE_OK) return s;
-    if (okind == 0) {
+    if (okind == 0 && !copied) {
         e = cudaMemcpyAsync(out, dout, grid_bytes, cudaMemcpyDeviceToHost, c->stream);
         if (e != cudaSuccess) return cuda_status(e);
     }

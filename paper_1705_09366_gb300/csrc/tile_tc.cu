@@ -265,11 +265,14 @@ __device__ __forceinline__ void drain_bar(uint32_t bar, uint32_t parity) {
         if (ptx::globaltimer() - t0 > DRAIN_NS) break;
 }
 
-__device__ __forceinline__ void decode_item(const Plan& pl, int64_t item, int& tx, int& ty,
+// Tile `item` of problem P's launch: ty fastest, then tx within the launch's tile
+// columns, then tb.
+__device__ __forceinline__ void decode_item(const ProblemDev& P, int64_t item, int& tx, int& ty,
                                             int& tb) {
-    ty = (int)(item % pl.nty);
-    tx = (int)((item / pl.nty) % pl.ntx);
-    tb = (int)(item / ((int64_t)pl.nty * pl.ntx));
+    const int ncx = P.ntxg > 0 ? P.ntxg : P.pl.ntx;
+    ty = (int)(item % P.pl.nty);
+    tx = P.tx0 + (int)((item / P.pl.nty) % ncx);
+    tb = (int)(item / ((int64_t)P.pl.nty * ncx));
 }
 
 // Problem of batch tile g: the last problem whose first tile is <= g.
@@ -483,7 +486,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             const uint32_t* __restrict__ start = P.start;
             const int64_t item = gk - P.item_base;  // tile of the problem
             int tx, ty, tb;
-            decode_item(pl, item, tx, ty, tb);
+            decode_item(P, item, tx, ty, tb);
             const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
             const int ncx = g.cx_hi - g.cx_lo + 1;
             const int nr = (g.s_hi >= g.s_lo && ncx > 0) ? (g.s_hi - g.s_lo + 1) * ncx : 0;
@@ -901,7 +904,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             const uint32_t touched = (uint32_t)dsc.w & 0xffu, drain = ((uint32_t)dsc.w >> 8) & 0xffu;
             const uint32_t stored = ((uint32_t)dsc.w >> 16) & 0xffu;
             int tx, ty, tb;
-            decode_item(pl, item, tx, ty, tb);
+            decode_item(P, item, tx, ty, tb);
             const int m = 32 * qtr + lane;
             const int X = tx * TX + m / TY, Y = ty * TY + m % TY, T0 = tb * NB;
             const int nbv = min(NB, pl.gt - T0);
@@ -980,7 +983,7 @@ __global__ void k_tile_cost(ProblemDev single, const ProblemDev* __restrict__ ta
     const Plan& pl = P.pl;
     const uint32_t* __restrict__ start = P.start;
     int tx, ty, tb;
-    decode_item(pl, i - P.item_base, tx, ty, tb);
+    decode_item(P, i - P.item_base, tx, ty, tb);
     const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
     uint32_t sum = 0;
     for (int s = g.s_lo; s <= g.s_hi; ++s)
@@ -1055,7 +1058,7 @@ size_t tile_order_bytes_items(int64_t items) {
 size_t tile_order_bytes(const Plan& pl) { return tile_order_bytes_items(tile_tc_items(pl)); }
 
 bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* tile_ctr,
-                    uint32_t* order_ws, int fp16, cudaStream_t st) {
+                    uint32_t* order_ws, int fp16, cudaStream_t st, int tx0, int ntxg) {
     ProblemDev single{};
     single.pl = pl;
     single.ev = b.ev;
@@ -1063,7 +1066,9 @@ bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* ti
     single.out = out;
     single.item_base = 0;
     single.evp = b.evp;
-    const int64_t items = tile_tc_items(pl);
+    single.tx0 = tx0;
+    single.ntxg = ntxg;
+    const int64_t items = ntxg > 0 ? tile_tc_items(pl) / pl.ntx * ntxg : tile_tc_items(pl);
     if (b.evp)
         return fp16 ? launch_cfg<true, true>(single, nullptr, 1, items, err, tile_ctr, order_ws, st)
                     : launch_cfg<false, true>(single, nullptr, 1, items, err, tile_ctr, order_ws, st);
