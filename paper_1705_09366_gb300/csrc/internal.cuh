@@ -28,7 +28,11 @@ struct Plan {
     float cs, ct, norm;
     // event binning: cells = xy tiles, slabs of `slab` voxels in T
     int ntx, nty, slab, nslab;
-    uint32_t nkeys;          // ntx*nty*nslab; key value nkeys marks an event that reaches no voxel
+    // bandwidth classes (per-event bandwidths only, else 1 x 1): class (a, b)
+    // holds the events with hsv_i <= hsv / 2^a and htv_i <= htv / 2^b, binned apart
+    // so that each class is read only around the tiles its own reach covers
+    int ncls_s, ncls_t;
+    uint32_t nkeys;          // classes*nslab*ntx*nty; key value nkeys marks an event that reaches no voxel
     int key_bits;
     // T blocks of the tile kernels
     int tblock, ntb;
@@ -69,9 +73,10 @@ struct Bins {
 
 // ----------------------------------------------------------------- prep.cu
 // K0: re-centre (FP64) and cast to FP32, compute each event's bin key.
+// evp: per-event bandwidth records in input order (their class joins the key), or NULL.
 void launch_recentre(const double* pts, int n, double x0, double y0, double t0, double sres,
                      double tres, const Plan& pl, float4* ev, uint32_t* keys, uint32_t* idx,
-                     int* err, cudaStream_t st);
+                     int* err, cudaStream_t st, const float4* evp = nullptr);
 // Stable LSD radix sort of (key, idx) pairs; result lands in keys/idx (tmp buffers used).
 size_t radix_sort_temp_bytes(int n);
 void launch_radix_sort(uint32_t* keys, uint32_t* idx, uint32_t* keys_tmp, uint32_t* idx_tmp,

@@ -14,14 +14,26 @@ namespace stkde {
 
 // ------------------------------------------------------------------- K0 ---
 
+// Bandwidth class of an event with record r = (hsv_i, htv_i, 1/hsv_i, 1/htv_i):
+// the largest (a, b) with hsv_i <= hsv / 2^a and htv_i <= htv / 2^b (a 10^-6
+// margin absorbs the rounding of the ratio), capped at the plan's class counts.
+__device__ __forceinline__ uint32_t bandwidth_class(const Plan& pl, float4 r) {
+    int a = 0, b = 0;
+    if (pl.ncls_s > 1) a = min(max(ilogbf(pl.hsv / r.x * (1.0f - 1.0e-6f)), 0), pl.ncls_s - 1);
+    if (pl.ncls_t > 1) b = min(max(ilogbf(pl.htv / r.y * (1.0f - 1.0e-6f)), 0), pl.ncls_t - 1);
+    return (uint32_t)(a * pl.ncls_t + b);
+}
+
 // Re-centres event i (row `row` of its problem's n x 3 array) and computes its
-// bin key, offset by the problem's first key.
+// bin key, offset by the problem's first key; with per-event bandwidth records
+// (evp, input order) the event's bandwidth class leads the key.
 __device__ __forceinline__ void recentre_one(const double* __restrict__ row, double x0, double y0,
                                              double t0, double sres, double tres, int by_recip,
                                              double isres, double itres, const Plan& pl,
                                              uint32_t key_base, int i, float4* __restrict__ ev,
                                              uint32_t* __restrict__ keys, uint32_t* __restrict__ idx,
-                                             int* __restrict__ err) {
+                                             int* __restrict__ err,
+                                             const float4* __restrict__ evp = nullptr) {
     const double x = row[0];
     const double y = row[1];
     const double t = row[2];
@@ -52,7 +64,9 @@ __device__ __forceinline__ void recentre_one(const double* __restrict__ row, dou
         const int cx = min(max((int)floorf(fx * (1.0f / TX)), 0), pl.ntx - 1);
         const int cy = min(max((int)floorf(fy * (1.0f / TY)), 0), pl.nty - 1);
         const int s = min(max((int)floorf(ft / (float)pl.slab), 0), pl.nslab - 1);
-        key = ((uint32_t)s * (uint32_t)pl.ntx + (uint32_t)cx) * (uint32_t)pl.nty + (uint32_t)cy;
+        const uint32_t cls = evp ? bandwidth_class(pl, evp[i]) : 0u;
+        key = (((cls * (uint32_t)pl.nslab + (uint32_t)s) * (uint32_t)pl.ntx + (uint32_t)cx) *
+               (uint32_t)pl.nty) + (uint32_t)cy;
     }
     ev[i] = make_float4(fx, fy, ft, __int_as_float(i));
     keys[i] = key_base + key;
@@ -63,21 +77,21 @@ __global__ void k_recentre(const double* __restrict__ pts, int n, double x0, dou
                            double t0, double sres, double tres, int by_recip, double isres,
                            double itres, Plan pl, float4* __restrict__ ev,
                            uint32_t* __restrict__ keys, uint32_t* __restrict__ idx,
-                           int* __restrict__ err) {
+                           int* __restrict__ err, const float4* __restrict__ evp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     recentre_one(pts + 3 * (size_t)i, x0, y0, t0, sres, tres, by_recip, isres, itres, pl, 0u, i,
-                 ev, keys, idx, err);
+                 ev, keys, idx, err, evp);
 }
 
 void launch_recentre(const double* pts, int n, double x0, double y0, double t0, double sres,
                      double tres, const Plan& pl, float4* ev, uint32_t* keys, uint32_t* idx,
-                     int* err, cudaStream_t st) {
+                     int* err, cudaStream_t st, const float4* evp) {
     if (n <= 0) return;
     int e;
     const bool p2 = (frexp(sres, &e) == 0.5) && (frexp(tres, &e) == 0.5);
     k_recentre<<<(n + 255) / 256, 256, 0, st>>>(pts, n, x0, y0, t0, sres, tres, p2 ? 1 : 0,
-                                               1.0 / sres, 1.0 / tres, pl, ev, keys, idx, err);
+                                               1.0 / sres, 1.0 / tres, pl, ev, keys, idx, err, evp);
 }
 
 // The same over a batch: event i belongs to the last problem whose ev_base <= i.

@@ -106,8 +106,9 @@ stkde_status check_problem(const double* points, int64_t n, const stkde_grid* g,
     return STKDE_OK;
 }
 
+// ncls_s x ncls_t bandwidth classes (per-event bandwidths; 1 x 1 otherwise).
 Plan make_plan(int kernel_constants, int64_t n, const stkde_grid* g, double hs, double ht,
-               int slab_opt) {
+               int slab_opt, int ncls_s = 1, int ncls_t = 1) {
     Plan p{};
     p.gx = (int)g->gx; p.gy = (int)g->gy; p.gt = (int)g->gt;
     const double hsv = hs / g->sres, htv = ht / g->tres;
@@ -120,17 +121,20 @@ Plan make_plan(int kernel_constants, int64_t n, const stkde_grid* g, double hs, 
     p.norm = n > 0 ? (float)(1.0 / ((double)n * hs * hs * ht)) : 0.0f;
     p.ntx = (p.gx + TX - 1) / TX;
     p.nty = (p.gy + TY - 1) / TY;
+    p.ncls_s = ncls_s;
+    p.ncls_t = ncls_t;
+    const uint64_t ncls = (uint64_t)ncls_s * (uint64_t)ncls_t;
     int slab = slab_opt > 0 ? slab_opt : 4;
     slab = slab < p.gt ? slab : p.gt;
     while (true) {
         const uint64_t ns = (uint64_t)((p.gt + slab - 1) / slab);
-        const uint64_t nk = ns * (uint64_t)p.ntx * (uint64_t)p.nty;
+        const uint64_t nk = ncls * ns * (uint64_t)p.ntx * (uint64_t)p.nty;
         if (nk <= MAX_KEYS || slab >= p.gt) break;
         slab *= 2;
     }
     p.slab = slab;
     p.nslab = (p.gt + slab - 1) / slab;
-    const uint64_t nk = (uint64_t)p.nslab * (uint64_t)p.ntx * (uint64_t)p.nty;
+    const uint64_t nk = ncls * (uint64_t)p.nslab * (uint64_t)p.ntx * (uint64_t)p.nty;
     p.nkeys = (uint32_t)(nk < 0xffffffffull ? nk : 0xffffffffull);
     int bits = 1;
     while (bits < 32 && ((uint64_t)1 << bits) <= (uint64_t)p.nkeys) ++bits;
@@ -190,7 +194,7 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
     const int n = pl.n;
     mark(c);
     launch_recentre(dpts, n, g->x0, g->y0, g->t0, g->sres, g->tres, pl, w.ev, w.keys, w.idx,
-                    c->d_err, st);
+                    c->d_err, st, evp);
     c->launches += 1;
     if (form == STKDE_FORM_SCATTER) {
         mark(c);
@@ -531,8 +535,18 @@ stkde_status stkde_compute_adaptive(stkde_ctx* c, const double* points, int64_t 
         }
         dout = c->out_tmp;
     }
-    const Plan pl = make_plan(c->opt.kernel_constants, n, g, hi[0], hi[1], c->opt.slab);
+    // Bandwidth classes for the tensor forms: halvings of the largest spatial
+    // bandwidth down to the smallest, at most 3, with 8-voxel T slabs (fewer,
+    // longer bin runs per tile).  Temporal classes are not used: a 256-voxel T
+    // block dwarfs the temporal reach, and each class multiplies the bin runs a
+    // tile walks.  The fp32 form walks its bins in block-synchronous batches, so
+    // more runs cost it more than the smaller reach saves: one class there.
     const bool tensor = c->opt.form != STKDE_FORM_FP32;
+    int ncls_s = 1;
+    if (tensor)
+        while (ncls_s < 3 && hi[0] / lo[0] > (double)(1 << ncls_s)) ++ncls_s;
+    const Plan pl = make_plan(c->opt.kernel_constants, n, g, hi[0], hi[1],
+                              c->opt.slab > 0 ? c->opt.slab : (ncls_s > 1 ? 8 : 0), ncls_s, 1);
     const size_t order_bytes = tensor ? tile_order_bytes(pl) : 0;
     const size_t nn = (size_t)n;
     // the problem's workspace, then staging for host bandwidths and the two

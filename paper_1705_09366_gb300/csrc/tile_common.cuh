@@ -15,7 +15,24 @@ struct TileGeom {
     int cx_lo, cx_hi, cy_lo, cy_hi, s_lo, s_hi;
 };
 
-__device__ __forceinline__ TileGeom tile_geom(const Plan& pl, int tx, int ty, int tb, int tblock) {
+// Bandwidth class `cls` of the plan (a = cls / ncls_t, b = cls % ncls_t) and its
+// reach in voxels: the class's largest possible bandwidths.
+__device__ __forceinline__ int plan_classes(const Plan& pl) { return pl.ncls_s * pl.ncls_t; }
+__device__ __forceinline__ float class_hsv(const Plan& pl, int cls) {
+    return ldexpf(pl.hsv, -(cls / pl.ncls_t));
+}
+__device__ __forceinline__ float class_htv(const Plan& pl, int cls) {
+    return ldexpf(pl.htv, -(cls % pl.ncls_t));
+}
+// First key of bin (class cls, slab s, cell x cx); cells y follow.
+__device__ __forceinline__ uint32_t bin_row(const Plan& pl, int cls, int s, int cx) {
+    return (((uint32_t)cls * (uint32_t)pl.nslab + (uint32_t)s) * (uint32_t)pl.ntx + (uint32_t)cx) *
+           (uint32_t)pl.nty;
+}
+
+// The tile with the reach (hsv, htv) of one bandwidth class.
+__device__ __forceinline__ TileGeom tile_geom_r(const Plan& pl, float hsv, float htv, int tx, int ty,
+                                                int tb, int tblock) {
     TileGeom g;
     g.X0 = tx * TX; g.X1 = min(g.X0 + TX, pl.gx);
     g.Y0 = ty * TY; g.Y1 = min(g.Y0 + TY, pl.gy);
@@ -23,14 +40,18 @@ __device__ __forceinline__ TileGeom tile_geom(const Plan& pl, int tx, int ty, in
     g.rx0 = (float)g.X0 + 0.5f; g.rx1 = (float)g.X1 - 0.5f;
     g.ry0 = (float)g.Y0 + 0.5f; g.ry1 = (float)g.Y1 - 0.5f;
     const float m = 0.01f;  // widen: binning only needs a superset
-    g.cx_lo = max(0, (int)floorf((g.rx0 - pl.hsv - m) * (1.0f / TX)));
-    g.cx_hi = min(pl.ntx - 1, (int)floorf((g.rx1 + pl.hsv + m) * (1.0f / TX)));
-    g.cy_lo = max(0, (int)floorf((g.ry0 - pl.hsv - m) * (1.0f / TY)));
-    g.cy_hi = min(pl.nty - 1, (int)floorf((g.ry1 + pl.hsv + m) * (1.0f / TY)));
-    const float t0 = (float)g.T0 + 0.5f - pl.htv - m, t1 = (float)g.T1 - 0.5f + pl.htv + m;
+    g.cx_lo = max(0, (int)floorf((g.rx0 - hsv - m) * (1.0f / TX)));
+    g.cx_hi = min(pl.ntx - 1, (int)floorf((g.rx1 + hsv + m) * (1.0f / TX)));
+    g.cy_lo = max(0, (int)floorf((g.ry0 - hsv - m) * (1.0f / TY)));
+    g.cy_hi = min(pl.nty - 1, (int)floorf((g.ry1 + hsv + m) * (1.0f / TY)));
+    const float t0 = (float)g.T0 + 0.5f - htv - m, t1 = (float)g.T1 - 0.5f + htv + m;
     g.s_lo = max(0, (int)floorf(t0 / (float)pl.slab));
     g.s_hi = min(pl.nslab - 1, (int)floorf(t1 / (float)pl.slab));
     return g;
+}
+
+__device__ __forceinline__ TileGeom tile_geom(const Plan& pl, int tx, int ty, int tb, int tblock) {
+    return tile_geom_r(pl, pl.hsv, pl.htv, tx, ty, tb, tblock);
 }
 
 // Does the cylinder of radius hsv and half-height htv (voxels) around the event

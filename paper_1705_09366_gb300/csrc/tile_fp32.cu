@@ -110,11 +110,15 @@ k_tile_fp32(Plan pl, const float4* __restrict__ ev, const float4* __restrict__ e
     };
 
     const uint32_t lt = (1u << lane) - 1u;
-    for (int s = g.s_lo; s <= g.s_hi; ++s) {
-        for (int cx = g.cx_lo; cx <= g.cx_hi; ++cx) {
-            const uint32_t kb = ((uint32_t)s * (uint32_t)pl.ntx + (uint32_t)cx) * (uint32_t)pl.nty;
-            const int a = (int)start[kb + g.cy_lo];
-            const int b = (int)start[kb + g.cy_hi + 1];
+    const int ncls = plan_classes(pl);
+    for (int cls = 0; cls < ncls; ++cls) {
+    // the bins of bandwidth class cls around the tile, within the class's reach
+    const TileGeom gc = ncls == 1 ? g : tile_geom_r(pl, class_hsv(pl, cls), class_htv(pl, cls), tx, ty, tb, F_TB);
+    for (int s = gc.s_lo; s <= gc.s_hi; ++s) {
+        for (int cx = gc.cx_lo; cx <= gc.cx_hi; ++cx) {
+            const uint32_t kb = bin_row(pl, cls, s, cx);
+            const int a = (int)start[kb + gc.cy_lo];
+            const int b = (int)start[kb + gc.cy_hi + 1];
             for (int base = a; base < b; base += F_THREADS) {
                 const int p = base + tid;
                 float4 e = make_float4(0.f, 0.f, 0.f, 0.f), bw = e;
@@ -158,6 +162,7 @@ k_tile_fp32(Plan pl, const float4* __restrict__ ev, const float4* __restrict__ e
                 __syncthreads();
             }
         }
+    }
     }
     const int rem = s_count;
     if (rem > 0) process(0, rem);

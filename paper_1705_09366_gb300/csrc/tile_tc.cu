@@ -487,7 +487,11 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             const int64_t item = gk - P.item_base;  // tile of the problem
             int tx, ty, tb;
             decode_item(P, item, tx, ty, tb);
-            const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
+            // the bins of each bandwidth class around the tile, within the class's reach
+            const int ncls = plan_classes(pl);
+            for (int cls = 0; cls < ncls && ok; ++cls) {
+            const TileGeom g = ncls == 1 ? tile_geom(pl, tx, ty, tb, NB)
+                                         : tile_geom_r(pl, class_hsv(pl, cls), class_htv(pl, cls), tx, ty, tb, NB);
             const int ncx = g.cx_hi - g.cx_lo + 1;
             const int nr = (g.s_hi >= g.s_lo && ncx > 0) ? (g.s_hi - g.s_lo + 1) * ncx : 0;
             for (int r0 = 0; r0 < nr && ok; r0 += 32) {
@@ -496,8 +500,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 const int r = r0 + lane;
                 if (r < nr) {
                     const int s = g.s_lo + r / ncx, cx = g.cx_lo + r % ncx;
-                    const uint32_t kb =
-                        ((uint32_t)s * (uint32_t)pl.ntx + (uint32_t)cx) * (uint32_t)pl.nty;
+                    const uint32_t kb = bin_row(pl, cls, s, cx);
                     a = start[kb + g.cy_lo];
                     len = start[kb + g.cy_hi + 1] - a;
                 }
@@ -528,6 +531,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                     done += take;
                     if (fill == (uint32_t)PEV) close_page(0, item, tx, ty, tb, pi, &pl);
                 }
+            }
             }
             if (!ok) break;
             if (!open && !(ok = open_page())) break;
@@ -984,13 +988,17 @@ __global__ void k_tile_cost(ProblemDev single, const ProblemDev* __restrict__ ta
     const uint32_t* __restrict__ start = P.start;
     int tx, ty, tb;
     decode_item(P, i - P.item_base, tx, ty, tb);
-    const TileGeom g = tile_geom(pl, tx, ty, tb, NB);
     uint32_t sum = 0;
-    for (int s = g.s_lo; s <= g.s_hi; ++s)
-        for (int cx = g.cx_lo; cx <= g.cx_hi; ++cx) {
-            const uint32_t kb = ((uint32_t)s * (uint32_t)pl.ntx + (uint32_t)cx) * (uint32_t)pl.nty;
-            sum += start[kb + g.cy_hi + 1] - start[kb + g.cy_lo];
-        }
+    const int ncls = plan_classes(pl);
+    for (int cls = 0; cls < ncls; ++cls) {
+        const TileGeom g = ncls == 1 ? tile_geom(pl, tx, ty, tb, NB)
+                                     : tile_geom_r(pl, class_hsv(pl, cls), class_htv(pl, cls), tx, ty, tb, NB);
+        for (int s = g.s_lo; s <= g.s_hi; ++s)
+            for (int cx = g.cx_lo; cx <= g.cx_hi; ++cx) {
+                const uint32_t kb = bin_row(pl, cls, s, cx);
+                sum += start[kb + g.cy_hi + 1] - start[kb + g.cy_lo];
+            }
+    }
     cost[i] = sum;
     atomicAdd(&hist[32 - __clz(sum)], 1u);
 }
