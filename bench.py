@@ -156,13 +156,13 @@ def tile_boxes(w, seed=0):
              min(w.gy, int(c % ny) * 8 + 8), 0, w.gt) for c in order]
 
 
-def oracle_sample(w, seconds, seed=0, calib=None, bw=None):
+def oracle_sample(w, seconds, seed=0, calib=None, bw=None, nthreads=0):
     """Times the FP64 oracle (Algorithm 2 on random tiles, all host cores) for
     about `seconds`, growing the sample in batches; returns (pairs, elapsed,
     boxes, results, seconds per box).  bw: per-event (hs, ht) arrays or None."""
     import oracle
     p = oracle.params(w.gx, w.gy, w.gt, w.hs, w.ht, x0=w.x0, y0=w.y0, t0=w.t0, sres=w.sres,
-                      tres=w.tres)
+                      tres=w.tres, nthreads=nthreads)
     boxes = tile_boxes(w, seed)
     done, pairs, elapsed, res = 0, 0, 0.0, []
     per_box = calib
@@ -278,22 +278,10 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    from paper_1705_09366_gb300 import replicas
 
     peaks, peaks_src = load_peaks()
-    w = synth.WORKLOADS[args.workload](seed_offset=rank)
+    w = synth.WORKLOADS[args.workload](seed_offset=replicas.instance_offset(rank))
     wname, hs_h, ht_h = workload_bandwidths(args, w, rank)
     adaptive = args.bandwidth == "adaptive"
     dims = (w.gx, w.gy, w.gt)
@@ -335,9 +323,9 @@ def run_ours(args):
     clk = clocks.stop() if rank == 0 else None
     ctx.synchronize()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = max_over_ranks(sum(step_ms) / 1000.0)
-    all_updates = sum_over_ranks(float(updates) * args.steps)
-    value = all_updates / total_s
+    # independent replicas: units of all ranks over the slowest rank's time
+    value, total_s, _ = replicas.job_throughput(dist, float(updates) * args.steps,
+                                                sum(step_ms) / 1000.0, dev)
     ms_per_step = 1000.0 * total_s / args.steps
 
     # ---- dominant kernel: library events around each phase (same stream)
@@ -364,6 +352,10 @@ def run_ours(args):
         roof["frac"] = roof["achieved"] / peak
         roof["note"] = (f"algorithmic FLOPs = 2 x {prods} products x {updates} voxel-point "
                         f"updates; peak = {peaks_src} dense bf16 (burst)")
+        # the same kernel against the FP32 CUDA-core roofline (one FMA per update)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp32_fma = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        roof["frac_of_fp32_fma_roofline"] = (updates / fp32_fma) / (tile_ms * 1e-3)
     else:
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak = 2.0 * 128 * sms * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -395,8 +387,9 @@ def run_ours(args):
             compute(ctx, hpts, hout, hhs, hht)
             ctx.synchronize()
         barrier()
-        e2e_s = max_over_ranks(time.perf_counter() - t)
-        e2e = {"value": sum_over_ranks(float(updates) * args.e2e_steps) / e2e_s, "unit": UNIT,
+        e2e_v, e2e_s, _ = replicas.job_throughput(dist, float(updates) * args.e2e_steps,
+                                                  time.perf_counter() - t, dev)
+        e2e = {"value": e2e_v, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": grid_bytes,
                "ms_per_step": 1e3 * e2e_s / args.e2e_steps}
         del hout, hpts
@@ -435,6 +428,11 @@ def run_ours(args):
         cpu = {"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"FP64 oracle (Algorithm 2) on {len(boxes)} random 16x8x{w.gt} tiles "
                          f"of the {wname} workload ({pairs} updates, {dt:.1f} s)"}
+        # one core, for comparison with the paper's sequential runs (Table 3)
+        p1, dt1, b1, _, _ = oracle_sample(w, min(3.0, args.cpu_seconds), seed=rank + 1,
+                                          bw=(hs_h, ht_h) if adaptive else None, nthreads=1)
+        cpu["single_core"] = {"value": p1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"{len(b1)} tiles, {p1} updates, {dt1:.1f} s"}
         scale = max(r.max() for r, _ in res)
         for f, buf in [(args.form, out)] + [(k, v["_out"]) for k, v in forms.items() if "_out" in v]:
             worst = 0.0
