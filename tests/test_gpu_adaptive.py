@@ -196,3 +196,41 @@ def test_update_count_matches_the_oracle(case):
     assert ref > 0
     assert got_dev == ref and got_host == ref
     assert same == fixed
+
+
+def _edge_cases():
+    rng = np.random.default_rng(zlib.crc32(b"adaptive-edges"))
+    cases = []
+    # one event, sub-voxel bandwidths
+    cases.append(("one-tiny", np.array([[10.3, 7.6, 4.4]]), np.array([0.7]), np.array([0.6]), (24, 20, 12)))
+    # events far outside the grid whose large cylinders reach in, beside small ones inside
+    far = np.array([[-30.0, 5.0, 10.0], [70.0, 40.0, 3.0], [20.0, -25.0, 60.0]])
+    near = synth.tiny(rng, 200, 40, 36, 50, spill=0.0)
+    pts = np.vstack([far, near])
+    hs = np.r_[np.array([34.0, 40.0, 30.0]), rng.uniform(0.8, 3.0, 200)]
+    ht = np.r_[np.array([12.0, 9.0, 15.0]), rng.uniform(0.8, 4.0, 200)]
+    cases.append(("far-reach", pts, hs, ht, (40, 36, 50)))
+    # a single time slice
+    pts = synth.tiny(rng, 300, 50, 30, 1, spill=0.2)
+    cases.append(("gt1", pts, rng.uniform(1.0, 8.0, 300), rng.uniform(0.3, 2.0, 300), (50, 30, 1)))
+    # bandwidths over a factor of 100 (more halvings than bandwidth classes)
+    pts = synth.tiny(rng, 800, 48, 40, 70, spill=0.1)
+    hs = np.where(rng.random(800) < 0.5, 0.3, 30.0) * rng.uniform(0.9, 1.1, 800)
+    ht = rng.uniform(0.5, 12.0, 800)
+    cases.append(("ratio-100", pts, hs, ht, (48, 40, 70)))
+    return cases
+
+
+@pytest.mark.parametrize("form", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("case", _edge_cases(), ids=lambda c: c[0])
+def test_adaptive_edge_cases(form, case):
+    name, pts, hs, ht, dims = case
+    p = oracle.params(*dims, 1.0, 1.0)
+    ref, slack = oracle.pb_adaptive(pts, hs, ht, p, with_slack=True)
+    with pkg.Context(form=form) as ctx:
+        out = ctx.compute_adaptive(torch.from_numpy(np.ascontiguousarray(pts)).cuda(), dims,
+                                   torch.from_numpy(hs).cuda(), torch.from_numpy(ht).cuda())
+        ctx.synchronize()
+        got = out.cpu().numpy()
+    assert ref.max() > 0, name
+    assert pu.excess_error(got, ref, slack) <= pu.TOL[form], name
