@@ -1018,15 +1018,18 @@ template <bool FP16, bool ADAPT>
 bool launch_cfg(const ProblemDev& single, const ProblemDev* table, int nprob, int64_t items,
                 int* err, int* tile_ctr, uint32_t* order_ws, cudaStream_t st) {
     auto kern = k_tile_tc<FP16, ADAPT>;
-    static bool attr = false;
-    if (!attr) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    // the shared-memory limit is raised once per device this process uses
+    constexpr int MAXDEV = 64;
+    static bool attr[MAXDEV] = {};
+    if (dev < 0 || dev >= MAXDEV) return false;
+    if (!attr[dev]) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::TOTAL) !=
             cudaSuccess)
             return false;
-        attr = true;
+        attr[dev] = true;
     }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (items <= 0) return true;
     if (items >= (int64_t)1 << 31) return false;  // the tile queue counts in int
