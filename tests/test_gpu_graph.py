@@ -7,7 +7,6 @@ stream) and replayed: each replay recomputes the grid from the current contents
 of the event buffer, bit-identical to a direct call.  Replays remove the host
 cost of the ~15 launches per call, which matters for small problems.
 """
-import numpy as np
 import pytest
 
 import paper_1705_09366_gb300 as pkg

@@ -4,10 +4,8 @@ Each rank draws its own instance (distinct seeds), and the whole-job
 throughput is the units of all ranks over the slowest rank's time, computed
 with the same helper bench.py uses under torchrun.
 """
-import os
 import socket
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
