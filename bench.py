@@ -54,7 +54,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(synth.WORKLOADS), default="large")
     ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "fp16x3", "fp32", "scatter"])
-    ap.add_argument("--compare", default="fp32,scatter",
+    ap.add_argument("--compare", default="fp16x3,fp32,scatter",
                     help="other forms timed beside the main one ('' for none)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
