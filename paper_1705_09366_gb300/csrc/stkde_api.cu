@@ -20,7 +20,7 @@ constexpr uint32_t MAX_KEYS = 1u << 25;
 // Host outputs of the tensor forms: the tile kernel runs in up to MAX_SLABS slabs
 // of X, each at least SLAB_MIN_BYTES of output, and each slab's copy to the host
 // overlaps the later slabs' kernels.
-constexpr int MAX_SLABS = 8;
+constexpr int MAX_SLABS = 16;
 constexpr size_t SLAB_MIN_BYTES = (size_t)64 << 20;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
