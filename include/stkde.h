@@ -89,7 +89,8 @@ typedef struct {
     void* stream;          /* cudaStream_t the work is ordered on; NULL = legacy default stream */
     int form;              /* stkde_form */
     int kernel_constants;  /* stkde_kernel_constants */
-    int t_block;           /* voxels of T per tile: 0 = automatic, else a multiple of 16, <= 256 */
+    int t_block;           /* reserved, must be 0 (tiles span 256 voxels of T in the tensor
+                              forms and 64 in the fp32 form) */
     int slab;              /* T extent of an event bin: 0 = automatic, else >= 1 */
     int profile;           /* 1: time each phase with CUDA events (see stkde_phase_times) */
 } stkde_options;

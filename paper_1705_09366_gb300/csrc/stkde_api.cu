@@ -351,8 +351,7 @@ stkde_status stkde_create(stkde_ctx** out, const stkde_options* opt) {
         return STKDE_ERR_INVALID_ARGUMENT;
     if (o.kernel_constants != STKDE_KERNEL_PRINTED && o.kernel_constants != STKDE_KERNEL_UNIT_MASS)
         return STKDE_ERR_INVALID_ARGUMENT;
-    if (o.t_block != 0 && (o.t_block < 16 || o.t_block > 256 || o.t_block % 16 != 0))
-        return STKDE_ERR_INVALID_ARGUMENT;
+    if (o.t_block != 0) return STKDE_ERR_INVALID_ARGUMENT;  // reserved
     if (o.slab < 0) return STKDE_ERR_INVALID_ARGUMENT;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return STKDE_ERR_UNSUPPORTED; }

@@ -75,9 +75,10 @@ def test_bad_options_are_rejected(libstkde):
     o = pkg.stkde_default_options()
     o.form = 17
     assert libstkde.stkde_create(ctypes.byref(h), ctypes.byref(o)) == pkg.ERR_INVALID_ARGUMENT
-    o = pkg.stkde_default_options()
-    o.t_block = 24
-    assert libstkde.stkde_create(ctypes.byref(h), ctypes.byref(o)) == pkg.ERR_INVALID_ARGUMENT
+    for tb in (24, 64):  # reserved field: only 0 is accepted
+        o = pkg.stkde_default_options()
+        o.t_block = tb
+        assert libstkde.stkde_create(ctypes.byref(h), ctypes.byref(o)) == pkg.ERR_INVALID_ARGUMENT
 
 
 def test_create_without_gpu_fails_cleanly(libstkde):
