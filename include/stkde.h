@@ -112,9 +112,12 @@ STKDE_API stkde_status stkde_create(stkde_ctx** ctx, const stkde_options* opt);
 /* Section 2.1 density of n events on `grid`, bandwidths hs and ht, written to
  * `out` (gx*gy*gt binary32, row-major [X][Y][T]).  `out` may be device memory
  * of the context's device or host memory; with host memory the result is
- * computed into a context-owned device buffer and copied back on the stream
- * (pinned memory: asynchronously; pageable memory: the call returns after the
- * copy).  `points` may be NULL only when n == 0.
+ * computed into a context-owned device buffer and copied back (pinned memory:
+ * asynchronously; pageable memory: the call returns after the copy).  With the
+ * tensor forms a host grid of at least 128 MB is computed in slabs along X and
+ * each slab is copied on a second stream while the later slabs compute; the
+ * context's stream waits for those copies.  `points` may be NULL only when
+ * n == 0.
  * Errors: INVALID_ARGUMENT (NULL pointers, n < 0 or n >= 2^31, non-positive or
  * non-finite hs, ht, sres, tres, a grid dimension < 1 or >= 2^31, or an
  * origin that is not finite), OOM (workspace), CUDA. */
