@@ -62,6 +62,11 @@ def parse_args():
     ap.add_argument("--bandwidth", choices=["fixed", "adaptive"], default="fixed",
                     help="adaptive: per-event bandwidths log-uniform in [h/spread, h*spread]")
     ap.add_argument("--spread", type=float, default=2.0)
+    ap.add_argument("--batch-count", type=int, default=64,
+                    help="instances of the batched workload timed beside the main line (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=600,
+                    help="requests of the serving run reported beside the main line (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
 
 
@@ -445,6 +450,13 @@ def run_ours(args):
     for v in forms.values():
         v.pop("_out", None)
 
+    # ---- batched workload and serving loop (rank 0, N = 1)
+    batch = serve = None
+    if rank == 0 and world == 1 and args.batch_count > 0:
+        batch = run_batch(pkg, torch, stream, args.form, args.batch_count)
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        serve = run_serve(args.form, args.serve_requests, args.serve_rate)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -465,6 +477,8 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "forms": forms,
+            "batch": batch,
+            "serve": serve,
             "max_rel_err": errs.get(args.form),
             "peaks": peaks_src,
         }
@@ -473,6 +487,54 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_batch(pkg, torch, stream, form, count):
+    """The batched workload: `count` uneven instances in one stkde_compute_batch
+    call against the same problems in one stkde_compute call each (CUDA events,
+    3 repetitions after 2 warm-up batches, no L2 flush: the instances are small)."""
+    ws = synth.batched(count=count)
+    pts = [torch.from_numpy(w.points).cuda() for w in ws]
+    outs = [torch.empty((w.gx, w.gy, w.gt), dtype=torch.float32, device="cuda") for w in ws]
+    probs = [(p, (w.gx, w.gy, w.gt), w.hs, w.ht, o) for p, w, o in zip(pts, ws, outs)]
+    with pkg.Context(stream=stream, form=form) as c:
+        for _ in range(2):
+            c.compute_batch(probs)
+        c.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(3):
+            c.compute_batch(probs)
+        s1.record(stream)
+        c.synchronize()
+        t_batch = s0.elapsed_time(s1) / 3
+        launches = c.last_launch_count()
+        s0.record(stream)
+        for _ in range(3):
+            for p, w, o in zip(pts, ws, outs):
+                c.compute(p, (w.gx, w.gy, w.gt), w.hs, w.ht, out=o)
+        s1.record(stream)
+        c.synchronize()
+        t_single = s0.elapsed_time(s1) / 3
+        updates = sum(c.count_updates(p, (w.gx, w.gy, w.gt), w.hs, w.ht) for p, w in zip(pts, ws))
+    return {"workload": f"{count} uneven instances (n log-uniform 1e3..5e5, grids 64^3..512x512x128)",
+            "events": int(sum(w.n for w in ws)), "voxels": int(sum(w.gx * w.gy * w.gt for w in ws)),
+            "updates": int(updates), "ms_per_batch": t_batch, "ms_single_calls": t_single,
+            "updates_per_s": updates / (t_batch * 1e-3), "launches_per_batch": launches}
+
+
+def run_serve(form, n_requests, rate):
+    """The serving loop over the resident sets: seeded Poisson arrivals, continuous
+    batching; latency = completion - arrival."""
+    from paper_1705_09366_gb300 import serve as srvmod
+
+    sets = synth.resident_sets()
+    srv = srvmod.Server(sets, form=form)
+    srv.run(srvmod.request_stream(8, 1000.0, len(sets), seed=99))
+    stats, _, _, _ = srv.run(srvmod.request_stream(n_requests, rate, len(sets), seed=0))
+    srv.close()
+    stats.update({"rate_hz": rate, "sets": [int(s.shape[0]) for s in sets]})
+    return stats
 
 
 def main():
