@@ -236,10 +236,21 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- ours ---
 
+def code_only(src: str) -> str:
+    """The source without // comments and blank lines: the key under which DRAM
+    counters are recorded, so that edits to the prose do not void them."""
+    lines = []
+    for ln in src.splitlines():
+        code = ln.split("//", 1)[0].rstrip()
+        if code:
+            lines.append(code)
+    return "\n".join(lines)
+
+
 def recorded_traffic(args):
     """DRAM bytes (read + write) of one tile-kernel launch from the committed ncu
     summary, if it was taken on this workload and form with the current kernel
-    source; else None."""
+    code (the source hashed without comments); else None."""
     if args.workload != "large" or args.form != "bf16x3" or args.bandwidth != "fixed":
         return None
     import hashlib
@@ -247,8 +258,8 @@ def recorded_traffic(args):
     src = os.path.join(ROOT, "paper_1705_09366_gb300", "csrc", "tile_tc.cu")
     if not (os.path.exists(prof) and os.path.exists(src)):
         return None
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
+    with open(src) as f:
+        sha = hashlib.sha256(code_only(f.read()).encode()).hexdigest()
     rec = {}
     with open(prof) as f:
         for ln in f:

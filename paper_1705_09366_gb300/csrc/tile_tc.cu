@@ -54,6 +54,11 @@
 // earlier entries, and the streams share only the epilogue, which never waits on
 // a stream's producers, so no wait can close a cycle.
 //
+// A launch covers all tiles of its problems, or (host outputs computed in slabs
+// along X) the tiles of a range of tile columns.  With per-event bandwidths the
+// events are binned by bandwidth class as well, and the loader walks each class's
+// bins within that class's own reach.
+//
 // With per-event bandwidths (ADAPT) a page holds 128 events followed by their
 // (hsv_i, htv_i, 1/hsv_i, 1/htv_i) records, both staged by the loader; the
 // filter and the column windows use each event's own bandwidths, the factor
