@@ -71,9 +71,12 @@ def lib():
         l.oracle_vb_adaptive.argtypes = [P, dp, dp, dp, i64, dp]
         l.oracle_pb_adaptive.argtypes = [P, dp, dp, dp, i64, dp, dp]
         l.oracle_pb_adaptive_boxes.argtypes = [P, dp, dp, dp, i64, dp, i64, dp, dp, dp]
+        l.oracle_abramson.argtypes = [P, dp, i64, dp, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, dp, dp, dp]
         for f in ("oracle_vb", "oracle_vb_voxels", "oracle_pb", "oracle_pb_box",
                   "oracle_pb_boxes", "oracle_count_updates", "oracle_max_threads",
-                  "oracle_vb_adaptive", "oracle_pb_adaptive", "oracle_pb_adaptive_boxes"):
+                  "oracle_vb_adaptive", "oracle_pb_adaptive", "oracle_pb_adaptive_boxes",
+                  "oracle_abramson"):
             getattr(l, f).restype = ctypes.c_int
         _lib = l
     return _lib
@@ -220,3 +223,20 @@ def pb_adaptive_boxes(points, hs, ht, p: Params, boxes, with_slack: bool = True,
         res.append((v, s_))
         off += sz
     return (res, npairs) if pair_counts else res
+
+
+def abramson(points, p: Params, alpha: float = 0.5, lam_min: float = 0.125, lam_max: float = 8.0,
+             pilot=None):
+    """Per-event bandwidths by Abramson's law from a pilot density with the fixed
+    pair (p.hs, p.ht) (computed here by PB unless given); returns (hs_i, ht_i, lambda_i)."""
+    a = _pts(points)
+    if pilot is None:
+        pilot = pb(a, p)
+    pil = np.ascontiguousarray(np.asarray(pilot, dtype=np.float64))
+    assert pil.shape == (p.gx, p.gy, p.gt)
+    n = a.shape[0]
+    hs, ht, lam = np.empty(n), np.empty(n), np.empty(n)
+    rc = lib().oracle_abramson(ctypes.byref(p), _ptr(a), n, _ptr(pil), float(alpha), float(lam_min),
+                               float(lam_max), _ptr(hs), _ptr(ht), _ptr(lam))
+    assert rc == 0
+    return hs, ht, lam

@@ -438,3 +438,51 @@ int oracle_pb_adaptive_boxes(const oracle_params* p, const double* pts, const do
     free(offs);
     return 0;
 }
+
+/* ------------------------------------------- bandwidths from a pilot grid --- */
+
+/* Per-event bandwidths that follow the population density (the adaptive
+ * bandwidth of the conclusion), by Abramson's square-root law: a pilot density
+ * f~ computed with the fixed pair (hs, ht) (p->hs, p->ht) is read at each
+ * event's voxel, X_i = floor((x_i - x0)/sres) clamped into the grid (likewise Y,
+ * T), floored at 1e-6 of the largest such value, and
+ *
+ *   lambda_i = clamp((f~_i / g)^(-alpha), lam_min, lam_max),
+ *   g = exp(mean_i log f~_i),   hs_i = hs lambda_i,   ht_i = ht lambda_i,
+ *
+ * so dense areas get narrower kernels; alpha = 1/2 is Abramson's choice.  pilot
+ * is the gx*gy*gt grid in the layout of oracle_pb; lam_out may be NULL. */
+int oracle_abramson(const oracle_params* p, const double* pts, int64_t n, const double* pilot,
+                    double alpha, double lam_min, double lam_max, double* hs_out, double* ht_out,
+                    double* lam_out) {
+    if (n <= 0) return 0;
+    double* f = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!f) return 1;
+    double fmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t X = (int64_t)floor((pts[3 * i + 0] - p->x0) / p->sres);
+        int64_t Y = (int64_t)floor((pts[3 * i + 1] - p->y0) / p->sres);
+        int64_t T = (int64_t)floor((pts[3 * i + 2] - p->t0) / p->tres);
+        X = X < 0 ? 0 : X >= p->gx ? p->gx - 1 : X;
+        Y = Y < 0 ? 0 : Y >= p->gy ? p->gy - 1 : Y;
+        T = T < 0 ? 0 : T >= p->gt ? p->gt - 1 : T;
+        f[i] = pilot[(X * p->gy + Y) * p->gt + T];
+        if (f[i] > fmax) fmax = f[i];
+    }
+    const double floor_f = 1e-6 * fmax;
+    double slog = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (f[i] < floor_f) f[i] = floor_f;
+        slog += log(f[i]);
+    }
+    const double g = exp(slog / (double)n);
+    for (int64_t i = 0; i < n; ++i) {
+        double lam = fmax > 0.0 ? pow(f[i] / g, -alpha) : 1.0;
+        lam = lam < lam_min ? lam_min : lam > lam_max ? lam_max : lam;
+        hs_out[i] = p->hs * lam;
+        ht_out[i] = p->ht * lam;
+        if (lam_out) lam_out[i] = lam;
+    }
+    free(f);
+    return 0;
+}

@@ -173,3 +173,71 @@ def test_box_pair_counts_equal_per_event_update_counts():
     ref = sum(oracle.count_updates(pts[i:i + 1], oracle.params(*dims, hs[i], ht[i], **kw))
               for i in range(n))
     assert int(counts.sum()) == ref
+
+
+# ---- bandwidths from a pilot density (Abramson's square-root law)
+
+def _clustered(seed, n=400, G=40):
+    rng = np.random.default_rng(seed)
+    return synth.clustered_events(rng, n, G, G, G, 3, (2.0, 6.0), (2.0, 6.0), 0.3), G
+
+
+def test_abramson_alpha_zero_gives_the_pilot_bandwidths():
+    pts, G = _clustered(1)
+    p = oracle.params(G, G, G, 3.0, 2.5)
+    hs, ht, lam = oracle.abramson(pts, p, alpha=0.0)
+    assert np.all(lam == 1.0) and np.all(hs == 3.0) and np.all(ht == 2.5)
+
+
+def test_abramson_geometric_mean_is_one():
+    """lambda_i = (f_i / g)^-alpha with g the geometric mean of the f_i: the
+    unclamped factors have geometric mean exactly 1."""
+    pts, G = _clustered(2)
+    p = oracle.params(G, G, G, 3.0, 2.5)
+    _, _, lam = oracle.abramson(pts, p, alpha=0.5, lam_min=1e-9, lam_max=1e9)
+    assert abs(np.exp(np.mean(np.log(lam))) - 1.0) < 1e-12
+
+
+def test_abramson_is_invariant_to_the_pilot_scale():
+    """Scaling the pilot (here: unit-mass instead of printed kernel constants)
+    leaves the factors unchanged."""
+    pts, G = _clustered(3)
+    a = oracle.abramson(pts, oracle.params(G, G, G, 3.0, 2.5), alpha=0.5)[2]
+    b = oracle.abramson(pts, oracle.params(G, G, G, 3.0, 2.5, cs=oracle.CS_UNIT_MASS), alpha=0.5)[2]
+    np.testing.assert_allclose(a, b, rtol=1e-12)
+
+
+def test_abramson_denser_means_narrower():
+    """The factor is a non-increasing function of the pilot value at the event's
+    voxel, with exponent -alpha."""
+    pts, G = _clustered(4)
+    p = oracle.params(G, G, G, 3.0, 2.5)
+    pilot = oracle.pb(pts, p)
+    _, _, lam = oracle.abramson(pts, p, alpha=0.5, lam_min=1e-9, lam_max=1e9, pilot=pilot)
+    vox = np.clip(np.floor(pts).astype(int), 0, G - 1)
+    f = pilot[vox[:, 0], vox[:, 1], vox[:, 2]]
+    f = np.maximum(f, 1e-6 * f.max())
+    order = np.argsort(f)
+    assert np.all(np.diff(lam[order]) <= 1e-15)
+    np.testing.assert_allclose(lam[order[-1]] / lam[order[0]], (f[order[-1]] / f[order[0]]) ** -0.5,
+                               rtol=1e-12)
+
+
+def test_abramson_cluster_against_a_lone_event():
+    """m coincident events and one lone event far away, same sub-voxel offset: the
+    pilot at the cluster is m times the pilot at the lone event, so the lone
+    event's factor is m^alpha times the cluster's, and the geometric mean is 1."""
+    m, G = 9, 48
+    # dyadic offsets: the binary32 re-centring keeps them exact
+    pts = np.array([[10.25, 10.625, 10.125]] * m + [[38.25, 37.625, 38.125]])
+    p = oracle.params(G, G, G, 4.0, 3.0)
+    _, _, lam = oracle.abramson(pts, p, alpha=0.5, lam_min=1e-9, lam_max=1e9)
+    assert lam[-1] / lam[0] == pytest.approx(m ** 0.5, rel=1e-12)
+    assert lam[0] ** m * lam[-1] == pytest.approx(1.0, rel=1e-12)
+
+
+def test_abramson_clamps():
+    pts, G = _clustered(5)
+    p = oracle.params(G, G, G, 3.0, 2.5)
+    _, _, lam = oracle.abramson(pts, p, alpha=1.0, lam_min=0.8, lam_max=1.25)
+    assert lam.min() == 0.8 and lam.max() == 1.25
