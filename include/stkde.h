@@ -173,6 +173,25 @@ STKDE_API stkde_status stkde_count_updates(stkde_ctx* ctx, const double* points,
                                  const stkde_grid* grid, double hs, double ht,
                                  uint64_t* count);
 
+/* Per-event bandwidths that follow the population density, for
+ * stkde_compute_adaptive: Abramson's square-root law on a pilot density.  The
+ * pilot is the density with the fixed pair (hs, ht), computed as by
+ * stkde_compute into `pilot` (device memory, gx*gy*gt binary32) or, when pilot is
+ * NULL, into a context-owned buffer.  It is read at each event's voxel
+ * (floor((x - x0)/sres) etc., clamped into the grid) and floored at 1e-6 of the
+ * largest such value, f_i; with g the geometric mean of the f_i,
+ *     lambda_i = clamp((f_i / g)^(-alpha), lam_min, lam_max),
+ *     hs_out[i] = hs lambda_i,   ht_out[i] = ht lambda_i
+ * (device memory, n doubles each).  alpha = 1/2 is Abramson's law, alpha = 0
+ * gives the fixed pair.  Dense areas get narrower kernels.  Errors:
+ * INVALID_ARGUMENT (as stkde_compute; alpha negative or not finite; lam_min not
+ * in (0, 1]; lam_max not finite or below 1; outputs or pilot not device memory),
+ * OOM, CUDA.  n = 0 leaves the outputs untouched (and zeroes a given pilot). */
+STKDE_API stkde_status stkde_abramson_bandwidths(stkde_ctx* ctx, const double* points, int64_t n,
+                                                 const stkde_grid* grid, double hs, double ht,
+                                                 double alpha, double lam_min, double lam_max,
+                                                 float* pilot, double* hs_out, double* ht_out);
+
 /* stkde_count_updates with per-event bandwidths hs, ht (as in
  * stkde_compute_adaptive): the pairs inside each event's own cylinder.
  * Synchronous.  Errors as stkde_compute_adaptive's INVALID_ARGUMENT cases. */

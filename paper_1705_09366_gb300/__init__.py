@@ -47,7 +47,7 @@ EXPORTED_SYMBOLS = (
     "stkde_default_options", "stkde_create", "stkde_compute", "stkde_compute_batch",
     "stkde_count_updates", "stkde_synchronize", "stkde_phase_times", "stkde_destroy",
     "stkde_status_string", "stkde_last_launch_count", "stkde_compute_static",
-    "stkde_compute_adaptive", "stkde_count_updates_adaptive",
+    "stkde_compute_adaptive", "stkde_count_updates_adaptive", "stkde_abramson_bandwidths",
 )
 
 STATIC_MAX_EVENTS = 262144
@@ -101,6 +101,9 @@ def lib():
         l.stkde_count_updates_adaptive.argtypes = [vp, vp, i64, ctypes.POINTER(Grid), vp, vp,
                                                    ctypes.POINTER(ctypes.c_uint64)]
         l.stkde_count_updates_adaptive.restype = ctypes.c_int
+        l.stkde_abramson_bandwidths.argtypes = [vp, vp, i64, ctypes.POINTER(Grid), dbl, dbl, dbl, dbl,
+                                                dbl, vp, vp, vp]
+        l.stkde_abramson_bandwidths.restype = ctypes.c_int
         l.stkde_compute_batch.restype = ctypes.c_int
         l.stkde_count_updates.argtypes = [vp, vp, i64, ctypes.POINTER(Grid), dbl, dbl,
                                           ctypes.POINTER(ctypes.c_uint64)]
@@ -199,6 +202,14 @@ def stkde_count_updates_adaptive(ctx, points, n: int, grid: Grid, hs, ht) -> int
                                               _ptr(hs), _ptr(ht), ctypes.byref(c)),
            "stkde_count_updates_adaptive")
     return int(c.value)
+
+
+def stkde_abramson_bandwidths(ctx, points, n: int, grid: Grid, hs: float, ht: float, alpha: float,
+                              lam_min: float, lam_max: float, pilot, hs_out, ht_out) -> None:
+    _check(lib().stkde_abramson_bandwidths(ctx, _ptr(points), int(n), ctypes.byref(grid), float(hs),
+                                           float(ht), float(alpha), float(lam_min), float(lam_max),
+                                           _ptr(pilot), _ptr(hs_out), _ptr(ht_out)),
+           "stkde_abramson_bandwidths")
 
 
 def stkde_compute_batch(ctx, problems) -> None:
@@ -302,6 +313,19 @@ class Context:
                                tres=1.0):
         g = make_grid(*dims, *origin, sres=sres, tres=tres)
         return stkde_count_updates_adaptive(self.handle, points, int(points.shape[0]), g, hs, ht)
+
+    def abramson_bandwidths(self, points, dims, hs, ht, alpha=0.5, lam_min=0.125, lam_max=8.0,
+                            pilot=None, origin=(0.0, 0.0, 0.0), sres=1.0, tres=1.0):
+        """Per-event bandwidths (hs_i, ht_i) from a pilot density with the fixed pair
+        (hs, ht) by Abramson's law; returns two (n,) float64 device tensors."""
+        import torch
+        n = int(points.shape[0])
+        hs_o = torch.empty(n, dtype=torch.float64, device=f"cuda:{self.device}")
+        ht_o = torch.empty(n, dtype=torch.float64, device=f"cuda:{self.device}")
+        g = make_grid(*dims, *origin, sres=sres, tres=tres)
+        stkde_abramson_bandwidths(self.handle, points, n, g, hs, ht, alpha, lam_min, lam_max, pilot,
+                                  hs_o, ht_o)
+        return hs_o, ht_o
 
     def compute_batch(self, problems):
         """Densities of several independent problems in one batched call.

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libstkde.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["stkde_api.cu", "prep.cu", "tile_fp32.cu", "scatter.cu", "tile_tc.cu", "static_path.cu"]
+SOURCES = ["stkde_api.cu", "prep.cu", "tile_fp32.cu", "scatter.cu", "tile_tc.cu", "static_path.cu",
+           "abramson.cu"]
 
 
 def nvcc() -> str:

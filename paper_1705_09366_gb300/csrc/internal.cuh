@@ -96,6 +96,17 @@ void launch_bandwidth_range(const double* h, int n, unsigned long long* range, c
 // ev_sorted[p] = ev[idx[p]] (the gather of launch_bounds_gather, for a second array).
 void launch_gather(const uint32_t* sorted_idx, const float4* ev, int n, float4* ev_sorted,
                    cudaStream_t st);
+// ---------------------------------------------------------- abramson.cu
+// Per-event bandwidths hs_i = hs lambda_i, ht_i = ht lambda_i from a pilot grid
+// (device, gx*gy*gt floats) by Abramson's square-root law (see abramson.cu);
+// events (device, n x 3) are read in input order.  scratch: abramson_scratch_bytes(n)
+// of device memory.  Returns the number of kernels launched.
+size_t abramson_scratch_bytes(int n);
+int launch_abramson(const double* pts, int n, double x0, double y0, double t0, double sres,
+                    double tres, int64_t gx, int64_t gy, int64_t gt, const float* pilot,
+                    double alpha, double lam_min, double lam_max, double hs, double ht,
+                    double* hs_out, double* ht_out, void* scratch, cudaStream_t st);
+
 // Exact update count (FP64 on the binary32 re-centred events, in input order).
 // hsv, htv: FP64 bandwidths in voxels; or per-event bandwidths hs, ht (domain
 // units, device memory, n each; NULL for the fixed pair) divided by sres, tres.

@@ -592,6 +592,63 @@ stkde_status stkde_compute_adaptive(stkde_ctx* c, const double* points, int64_t 
     return cuda_status(cudaGetLastError());
 }
 
+// Bandwidths from a pilot density: the pilot is stkde_compute with the fixed pair
+// into `pilot` (or the context's result buffer), then five small kernels sample it
+// at the events, reduce, and write hs_i, ht_i.
+stkde_status stkde_abramson_bandwidths(stkde_ctx* c, const double* points, int64_t n,
+                                       const stkde_grid* g, double hs, double ht, double alpha,
+                                       double lam_min, double lam_max, float* pilot,
+                                       double* hs_out, double* ht_out) {
+    if (!c || !g) return STKDE_ERR_INVALID_ARGUMENT;
+    stkde_status s = check_problem(points, n, g, hs, ht);
+    if (s != STKDE_OK) return s;
+    if (!(isfinite(alpha) && alpha >= 0.0) || !(lam_min > 0.0 && lam_min <= 1.0) ||
+        !(isfinite(lam_max) && lam_max >= 1.0))
+        return STKDE_ERR_INVALID_ARGUMENT;
+    if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
+    if (pilot && pointer_kind(pilot, c->device) != 1) return STKDE_ERR_INVALID_ARGUMENT;
+    if (n == 0) return pilot ? stkde_compute(c, points, 0, g, hs, ht, pilot) : STKDE_OK;
+    if (!hs_out || !ht_out || pointer_kind(hs_out, c->device) != 1 ||
+        pointer_kind(ht_out, c->device) != 1)
+        return STKDE_ERR_INVALID_ARGUMENT;
+    const int pkind = pointer_kind(points, c->device);
+    if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
+    const size_t grid_bytes = sizeof(float) * (size_t)g->gx * (size_t)g->gy * (size_t)g->gt;
+    float* dpil = pilot;
+    if (!dpil) {  // the context's result buffer holds the pilot
+        if (grid_bytes > c->out_tmp_bytes) {
+            cudaStreamSynchronize(c->stream);
+            if (c->out_tmp) cudaFree(c->out_tmp);
+            c->out_tmp = nullptr; c->out_tmp_bytes = 0;
+            if (cudaMalloc(&c->out_tmp, grid_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return STKDE_ERR_OOM;
+            }
+            c->out_tmp_bytes = grid_bytes;
+        }
+        dpil = c->out_tmp;
+    }
+    s = stkde_compute(c, points, n, g, hs, ht, dpil);
+    if (s != STKDE_OK) return s;
+    const int launches = c->launches;
+    // the workspace after the pilot's work (same stream): events (if host) and scratch
+    const size_t o_pts = 0, o_scr = align_up(pkind == 0 ? 24 * (size_t)n : 0, 256);
+    s = ensure_ws(c, o_scr + abramson_scratch_bytes((int)n));
+    if (s != STKDE_OK) return s;
+    char* wb = static_cast<char*>(c->ws);
+    const double* dpts = points;
+    if (pkind == 0) {
+        cudaError_t e = cudaMemcpyAsync(wb + o_pts, points, 24 * (size_t)n, cudaMemcpyHostToDevice,
+                                        c->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        dpts = reinterpret_cast<const double*>(wb + o_pts);
+    }
+    c->launches = launches + launch_abramson(dpts, (int)n, g->x0, g->y0, g->t0, g->sres, g->tres,
+                                             g->gx, g->gy, g->gt, dpil, alpha, lam_min, lam_max,
+                                             hs, ht, hs_out, ht_out, wb + o_scr, c->stream);
+    return cuda_status(cudaGetLastError());
+}
+
 // Batched compute: one re-centre, one binning sort and one bounds + gather pass
 // over the concatenated events of all problems (keys offset per problem, so the
 // sort groups events by problem, then by bin), then one tile-kernel launch whose
