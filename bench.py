@@ -16,7 +16,8 @@ data; the only collectives are the barrier and the max-over-ranks of the time.
 ``--impl reference`` times the FP64 CPU oracle (the paper has no GPU code) on a
 bounded sample of tiles of the same workload.  ``--bandwidth adaptive`` gives
 every event its own bandwidths (log-uniform in [h/spread, h*spread] around the
-workload's pair) and times stkde_compute_adaptive instead.
+workload's pair) and times stkde_compute_adaptive instead; ``--bandwidth abramson``
+takes them from stkde_abramson_bandwidths (a pilot density by Abramson's law).
 """
 from __future__ import annotations
 
@@ -59,8 +60,10 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--bandwidth", choices=["fixed", "adaptive"], default="fixed",
-                    help="adaptive: per-event bandwidths log-uniform in [h/spread, h*spread]")
+    ap.add_argument("--bandwidth", choices=["fixed", "adaptive", "abramson"], default="fixed",
+                    help="adaptive: per-event bandwidths log-uniform in [h/spread, h*spread]; "
+                         "abramson: from a pilot density by Abramson's law, factors clamped "
+                         "to [1/spread, spread]")
     ap.add_argument("--spread", type=float, default=2.0)
     ap.add_argument("--batch-count", type=int, default=64,
                     help="instances of the batched workload timed beside the main line (0: skip)")
@@ -70,12 +73,35 @@ def parse_args():
     return ap.parse_args()
 
 
-def workload_bandwidths(args, w, seed):
-    """(name, hs, ht): the workload's fixed pair, or per-event arrays."""
+def workload_bandwidths(args, w, seed, ctx=None, pts=None):
+    """(name, hs, ht): the workload's fixed pair, or per-event arrays (host).  The
+    Abramson bandwidths come from the library (ctx, device events) or, without a
+    context, from the FP64 oracle."""
     if args.bandwidth == "fixed":
         return w.name, w.hs, w.ht
+    if args.bandwidth == "abramson":
+        lo, hi = 1.0 / args.spread, args.spread
+        if ctx is not None:
+            hs, ht = ctx.abramson_bandwidths(pts, (w.gx, w.gy, w.gt), w.hs, w.ht, alpha=0.5,
+                                             lam_min=lo, lam_max=hi)
+            ctx.synchronize()
+            hs, ht = hs.cpu().numpy(), ht.cpu().numpy()
+        else:
+            import oracle
+            p = oracle.params(w.gx, w.gy, w.gt, w.hs, w.ht)
+            hs, ht, _ = oracle.abramson(w.points, p, alpha=0.5, lam_min=lo, lam_max=hi)
+        return f"{w.name}-abramson-x{args.spread:g}", hs, ht
     hs, ht = synth.adaptive_bandwidths(w.n, w.hs, w.ht, spread=args.spread, seed=seed)
     return f"{w.name}-adaptive-x{args.spread:g}", hs, ht
+
+
+def bandwidth_label(args):
+    if args.bandwidth == "adaptive":
+        return f"per event, log-uniform in [h/{args.spread:g}, h*{args.spread:g}]"
+    if args.bandwidth == "abramson":
+        return (f"per event, Abramson's law (alpha 1/2) on the fixed-pair pilot, factors in "
+                f"[1/{args.spread:g}, {args.spread:g}]")
+    return "fixed"
 
 
 def load_peaks():
@@ -297,11 +323,12 @@ def run_ours(args):
 
     peaks, peaks_src = load_peaks()
     w = synth.WORKLOADS[args.workload](seed_offset=replicas.instance_offset(rank))
-    wname, hs_h, ht_h = workload_bandwidths(args, w, rank)
-    adaptive = args.bandwidth == "adaptive"
+    adaptive = args.bandwidth != "fixed"
     dims = (w.gx, w.gy, w.gt)
     stream = torch.cuda.current_stream(dev)
     pts = torch.from_numpy(w.points).to(dev)
+    with pkg.Context(device=local, stream=stream, form=args.form) as bctx:
+        wname, hs_h, ht_h = workload_bandwidths(args, w, rank, bctx, pts)
     hs_d = torch.from_numpy(hs_h).to(dev) if adaptive else w.hs
     ht_d = torch.from_numpy(ht_h).to(dev) if adaptive else w.ht
     out = torch.empty(dims, dtype=torch.float32, device=dev)
@@ -476,8 +503,7 @@ def run_ours(args):
             "dtype": {"bf16x3": "bf16", "fp16x3": "f16", "fp32": "f32", "scatter": "f32"}[args.form],
             "data": "synthetic",
             "config": {"workload": wname, "n": w.n, "grid": [w.gx, w.gy, w.gt], "hs": w.hs,
-                       "ht": w.ht, "bandwidth": args.bandwidth if not adaptive else
-                       f"per event, log-uniform in [h/{args.spread:g}, h*{args.spread:g}]",
+                       "ht": w.ht, "bandwidth": bandwidth_label(args),
                        "form": args.form, "updates_per_grid": updates,
                        "l2": "flushed before each step (256 MiB write); output 2.1 GB > L2",
                        "parallelism": f"{world} independent instance(s), one per GPU"},
