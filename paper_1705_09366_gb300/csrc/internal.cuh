@@ -125,7 +125,7 @@ void launch_scatter(const Plan& pl, const float4* ev, float* out, cudaStream_t s
 int64_t tile_tc_items(const Plan& pl);
 size_t tile_order_bytes(const Plan& pl);
 size_t tile_order_bytes_items(int64_t items);
-// Returns false if the form is not available in this build (or the problem has
+// Returns false if the form is not compiled into the library (or the problem has
 // 2^31 tiles or more).  tile_ctr: one device int, the launch's tile queue (zeroed
 // here on the stream before the kernel).  order_ws: tile_order_bytes(pl) of device
 // scratch for the heaviest-first tile order (two extra launches), or NULL to take
