@@ -155,9 +155,9 @@ STKDE_API stkde_status stkde_compute_batch(stkde_ctx* ctx, const stkde_problem* 
  * inclusive), so hs[i] = hs, ht[i] = ht for all i gives stkde_compute's density.
  * hs, ht: n doubles each, domain units, host or device memory (each on its
  * own); points, grid and out as in stkde_compute.  Event binning and tile reach
- * use the largest bandwidths, so a few very large ones slow every tile.  With
- * device bandwidth arrays the call waits for the stream once, to read their
- * range.  Errors: INVALID_ARGUMENT (as stkde_compute; a NULL hs or ht with
+ * use the largest bandwidths, so a few very large ones slow every tile.  The
+ * call waits for the stream once, to read the bandwidth range (host arrays are
+ * first copied into a context-owned device buffer).  Errors: INVALID_ARGUMENT (as stkde_compute; a NULL hs or ht with
  * n > 0; a bandwidth that is not finite and positive, or hs[i]/sres or
  * ht[i]/tres >= 1e6), UNSUPPORTED (the scatter form; the fp16x3 form when
  * (max hs / min hs)^2 (max ht / min ht) > 2^14, where its weighted operand

@@ -40,6 +40,8 @@ struct stkde_ctx {
     int* d_ctr = nullptr;  // tile queue of the tensor tile kernel
     unsigned long long* d_count = nullptr;
     unsigned long long* d_range = nullptr;  // bandwidth range of stkde_compute_adaptive (2 x 3 words)
+    double* bw_stage = nullptr;             // device copies of host bandwidth arrays
+    size_t bw_stage_bytes = 0;
     cudaEvent_t ev[MAX_PHASES + 1];
     int nphase = 0;
     bool events_ok = false;
@@ -267,41 +269,57 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
     return cuda_status(cudaGetLastError());
 }
 
-// Smallest and largest of the per-event bandwidth arrays hs, ht (kind 1: device
-// memory, read by a reduction kernel and one wait for the stream; else host
-// memory, read here); INVALID_ARGUMENT if one is not finite and positive.
-stkde_status bandwidth_range(stkde_ctx* c, int64_t n, const double* hs, const double* ht,
-                             int hkind, int tkind, double lo[2], double hi[2]) {
-    const double* arr[2] = {hs, ht};
-    const int kind[2] = {hkind, tkind};
-    bool bad = false;
-    if (hkind == 1 || tkind == 1) {
-        unsigned long long init[6] = {~0ull, 0ull, 0ull, ~0ull, 0ull, 0ull};
-        cudaError_t e = cudaMemcpyAsync(c->d_range, init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
-        if (e != cudaSuccess) return cuda_status(e);
-        for (int a = 0; a < 2; ++a)
-            if (kind[a] == 1) launch_bandwidth_range(arr[a], (int)n, c->d_range + 3 * a, c->stream);
-        unsigned long long got[6];
-        e = cudaMemcpyAsync(got, c->d_range, sizeof(got), cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) return cuda_status(e);
-        for (int a = 0; a < 2; ++a) {
-            if (kind[a] != 1) continue;
-            bad = bad || got[3 * a + 2] != 0;
-            memcpy(&lo[a], &got[3 * a], sizeof(double));
-            memcpy(&hi[a], &got[3 * a + 1], sizeof(double));
+// Device copies of the per-event bandwidth arrays: device arrays are used in
+// place, host arrays (kind 0) are copied on the stream into the context's staging
+// buffer, which grows on demand.
+stkde_status stage_bandwidths(stkde_ctx* c, int64_t n, const double*& hs, const double*& ht,
+                              int hkind, int tkind) {
+    const size_t nn = (size_t)n;
+    const size_t need = sizeof(double) * ((hkind == 0 ? nn : 0) + (tkind == 0 ? nn : 0));
+    if (need == 0) return STKDE_OK;
+    if (need > c->bw_stage_bytes) {
+        cudaStreamSynchronize(c->stream);
+        if (c->bw_stage) cudaFree(c->bw_stage);
+        c->bw_stage = nullptr; c->bw_stage_bytes = 0;
+        if (cudaMalloc(&c->bw_stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            return STKDE_ERR_OOM;
         }
+        c->bw_stage_bytes = need;
     }
+    double* dst = c->bw_stage;
+    cudaError_t e = cudaSuccess;
+    if (hkind == 0) {
+        e = cudaMemcpyAsync(dst, hs, sizeof(double) * nn, cudaMemcpyHostToDevice, c->stream);
+        hs = dst;
+        dst += nn;
+    }
+    if (e == cudaSuccess && tkind == 0) {
+        e = cudaMemcpyAsync(dst, ht, sizeof(double) * nn, cudaMemcpyHostToDevice, c->stream);
+        ht = dst;
+    }
+    return cuda_status(e);
+}
+
+// Smallest and largest of the per-event bandwidth arrays hs, ht (device memory):
+// a reduction kernel per array and one wait for the stream; INVALID_ARGUMENT if
+// one is not finite and positive.
+stkde_status bandwidth_range(stkde_ctx* c, int64_t n, const double* hs, const double* ht,
+                             double lo[2], double hi[2]) {
+    const double* arr[2] = {hs, ht};
+    unsigned long long init[6] = {~0ull, 0ull, 0ull, ~0ull, 0ull, 0ull};
+    cudaError_t e = cudaMemcpyAsync(c->d_range, init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int a = 0; a < 2; ++a) launch_bandwidth_range(arr[a], (int)n, c->d_range + 3 * a, c->stream);
+    unsigned long long got[6];
+    e = cudaMemcpyAsync(got, c->d_range, sizeof(got), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    bool bad = false;
     for (int a = 0; a < 2; ++a) {
-        if (kind[a] == 1) continue;
-        lo[a] = INFINITY;
-        hi[a] = 0.0;
-        for (int64_t i = 0; i < n; ++i) {
-            const double v = arr[a][i];
-            if (!finite_pos(v)) { bad = true; break; }
-            lo[a] = v < lo[a] ? v : lo[a];
-            hi[a] = v > hi[a] ? v : hi[a];
-        }
+        bad = bad || got[3 * a + 2] != 0;
+        memcpy(&lo[a], &got[3 * a], sizeof(double));
+        memcpy(&hi[a], &got[3 * a + 1], sizeof(double));
     }
     return bad ? STKDE_ERR_INVALID_ARGUMENT : STKDE_OK;
 }
@@ -401,6 +419,7 @@ void stkde_destroy(stkde_ctx* c) {
     if (c->d_ctr) cudaFree(c->d_ctr);
     if (c->d_count) cudaFree(c->d_count);
     if (c->d_range) cudaFree(c->d_range);
+    if (c->bw_stage) cudaFree(c->bw_stage);
     for (int i = 0; i <= MAX_PHASES; ++i)
         if (c->events_ok) cudaEventDestroy(c->ev[i]);
     if (c->copy_stream) {
@@ -509,8 +528,12 @@ stkde_status stkde_compute_adaptive(stkde_ctx* c, const double* points, int64_t 
     const int hkind = pointer_kind(hs, c->device), tkind = pointer_kind(ht, c->device);
     if (okind < 0 || pkind < 0 || hkind < 0 || tkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
 
+    const double* dhs = hs;
+    const double* dht = ht;
+    s = stage_bandwidths(c, n, dhs, dht, hkind, tkind);
+    if (s != STKDE_OK) return s;
     double lo[2], hi[2];
-    s = bandwidth_range(c, n, hs, ht, hkind, tkind, lo, hi);
+    s = bandwidth_range(c, n, dhs, dht, lo, hi);
     if (s != STKDE_OK) return s;
     s = check_problem(points, n, g, hi[0], hi[1]);
     if (s != STKDE_OK) return s;
@@ -548,32 +571,20 @@ stkde_status stkde_compute_adaptive(stkde_ctx* c, const double* points, int64_t 
                               c->opt.slab > 0 ? c->opt.slab : (ncls_s > 1 ? 8 : 0), ncls_s, 1);
     const size_t order_bytes = tensor ? tile_order_bytes(pl) : 0;
     const size_t nn = (size_t)n;
-    // the problem's workspace, then staging for host bandwidths and the two
-    // bandwidth record arrays
+    // the problem's workspace, then the two bandwidth record arrays
     const size_t base = carve(nullptr, (int)n, pl.nkeys, pkind == 0, order_bytes, nullptr);
-    const size_t o_hs = base, o_ht = align_up(o_hs + (hkind == 0 ? 8 * nn : 0), 256);
-    const size_t o_evp = align_up(o_ht + (tkind == 0 ? 8 * nn : 0), 256);
+    const size_t o_evp = align_up(base, 256);
     const size_t o_evps = align_up(o_evp + 16 * nn, 256);
     s = ensure_ws(c, align_up(o_evps + 16 * nn, 256));
     if (s != STKDE_OK) return s;
     Workspace w;
     carve(c->ws, (int)n, pl.nkeys, pkind == 0, order_bytes, &w);
     char* wb = static_cast<char*>(c->ws);
-    const double* dhs = hs;
-    const double* dht = ht;
     cudaError_t e = cudaSuccess;
     c->nphase = 0;
     c->launches = 0;
-    if (hkind == 0) {
-        e = cudaMemcpyAsync(wb + o_hs, hs, 8 * nn, cudaMemcpyHostToDevice, c->stream);
-        dhs = reinterpret_cast<const double*>(wb + o_hs);
-    }
-    if (e == cudaSuccess && tkind == 0) {
-        e = cudaMemcpyAsync(wb + o_ht, ht, 8 * nn, cudaMemcpyHostToDevice, c->stream);
-        dht = reinterpret_cast<const double*>(wb + o_ht);
-    }
     const double* dpts = points;
-    if (e == cudaSuccess && pkind == 0) {
+    if (pkind == 0) {
         e = cudaMemcpyAsync(w.pts, points, 24 * nn, cudaMemcpyHostToDevice, c->stream);
         dpts = w.pts;
     }
@@ -583,7 +594,7 @@ stkde_status stkde_compute_adaptive(stkde_ctx* c, const double* points, int64_t 
     launch_bandwidths(dhs, dht, (int)n, g->sres, g->tres, evp, c->stream);
     bool copied = false;
     s = enqueue(c, dpts, pl, g, w, dout, evp, evps, okind == 0 ? out : nullptr, &copied);
-    c->launches += 1 + (hkind == 1) + (tkind == 1);
+    c->launches += 3;  // two range reductions and the record conversion
     if (s != STKDE_OK) return s;
     if (okind == 0 && !copied) {
         e = cudaMemcpyAsync(out, dout, grid_bytes, cudaMemcpyDeviceToHost, c->stream);
@@ -856,12 +867,14 @@ stkde_status stkde_count_updates_adaptive(stkde_ctx* c, const double* points, in
     if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
     const int hkind = pointer_kind(hs, c->device), tkind = pointer_kind(ht, c->device);
     if (hkind < 0 || tkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
+    s = stage_bandwidths(c, n, hs, ht, hkind, tkind);
+    if (s != STKDE_OK) return s;
     double lo[2], hi[2];
-    s = bandwidth_range(c, n, hs, ht, hkind, tkind, lo, hi);
+    s = bandwidth_range(c, n, hs, ht, lo, hi);
     if (s != STKDE_OK) return s;
     s = check_problem(points, n, g, hi[0], hi[1]);
     if (s != STKDE_OK) return s;
-    return count_updates(c, points, n, g, hi[0], hi[1], hs, ht, hkind, tkind, count);
+    return count_updates(c, points, n, g, hi[0], hi[1], hs, ht, 1, 1, count);
 }
 
 int stkde_last_launch_count(stkde_ctx* c) { return c ? c->launches : 0; }
