@@ -59,7 +59,9 @@ typedef enum {
     STKDE_ERR_CUDA = 3,             /* a CUDA runtime call failed */
     STKDE_ERR_TIMEOUT = 4,          /* a device-side bounded wait gave up */
     STKDE_ERR_UNSUPPORTED = 5,      /* e.g. no sm_103a device, or a form not built */
-    STKDE_ERR_NONFINITE = 6         /* an event coordinate was NaN or infinite */
+    STKDE_ERR_NONFINITE = 6,        /* an event coordinate was NaN or infinite */
+    STKDE_ERR_INTERNAL = 7          /* a device-side consistency check refused an operation (an
+                                       accumulator window outside its tile); the grid is not valid */
 } stkde_status;
 
 /* How the sum over events is evaluated.  Every form writes each voxel of the
@@ -75,7 +77,14 @@ typedef enum {
     /* plain port of Algorithm 3: one block per event, atomic adds into a
      * zeroed grid.  Baseline only: the summation order, and so the last bits,
      * vary from run to run. */
-    STKDE_FORM_SCATTER = 3
+    STKDE_FORM_SCATTER = 3,
+    /* tcgen05 tensor cores, kind::tf32: hi = the value with its low 13
+     * significand bits cleared, lo = the remainder; three products (hi*hi +
+     * hi*lo + lo*hi), fp32 accumulation in tensor memory.  Fixed bandwidths only. */
+    STKDE_FORM_TENSOR_TF32X3 = 4,
+    /* one tf32 product per term (hi*hi): about 2^-11 relative error per term,
+     * for comparison only.  Fixed bandwidths only. */
+    STKDE_FORM_TENSOR_TF32X1 = 5
 } stkde_form;
 
 /* Kernel constants (Section 2.1). */

@@ -18,8 +18,8 @@ __all__ = [
     "Options", "Grid", "Problem", "StkdeError", "Context", "lib", "lib_path",
     "stkde_default_options", "stkde_create", "stkde_compute", "stkde_compute_batch",
     "stkde_count_updates", "stkde_synchronize", "stkde_phase_times", "stkde_destroy",
-    "stkde_status_string", "stkde_last_launch_count", "stkde_compute_static", "FORM_TENSOR_BF16X3", "FORM_TENSOR_FP16X3", "FORM_FP32",
-    "FORM_SCATTER", "KERNEL_PRINTED", "KERNEL_UNIT_MASS", "EXPORTED_SYMBOLS",
+    "stkde_status_string", "stkde_last_launch_count", "stkde_compute_static", "FORM_TENSOR_BF16X3",
+    "FORM_TENSOR_FP16X3", "FORM_FP32", "FORM_SCATTER", "FORM_TENSOR_TF32X3", "FORM_TENSOR_TF32X1", "KERNEL_PRINTED", "KERNEL_UNIT_MASS", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -32,13 +32,16 @@ ERR_CUDA = 3
 ERR_TIMEOUT = 4
 ERR_UNSUPPORTED = 5
 ERR_NONFINITE = 6
+ERR_INTERNAL = 7
 
 FORM_TENSOR_BF16X3 = 0
 FORM_TENSOR_FP16X3 = 1
 FORM_FP32 = 2
 FORM_SCATTER = 3
+FORM_TENSOR_TF32X3 = 4
+FORM_TENSOR_TF32X1 = 5
 FORMS = {"bf16x3": FORM_TENSOR_BF16X3, "fp16x3": FORM_TENSOR_FP16X3, "fp32": FORM_FP32,
-         "scatter": FORM_SCATTER}
+         "scatter": FORM_SCATTER, "tf32x3": FORM_TENSOR_TF32X3, "tf32x1": FORM_TENSOR_TF32X1}
 
 KERNEL_PRINTED = 0
 KERNEL_UNIT_MASS = 1

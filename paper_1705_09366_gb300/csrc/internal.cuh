@@ -132,14 +132,15 @@ size_t tile_order_bytes_items(int64_t items);
 // the tiles in index order.
 // tx0, ntxg: only the tiles of tile columns tx0 .. tx0 + ntxg - 1 (ntxg 0: all), so
 // that a grid can be computed in slabs of X whose copies overlap later slabs.
+// form: 0 bf16x3, 1 fp16x3, 2 tf32x3, 3 tf32x1 (the last two with fixed bandwidths only).
 bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* tile_ctr,
-                    uint32_t* order_ws, int fp16, cudaStream_t st, int tx0 = 0, int ntxg = 0);
+                    uint32_t* order_ws, int form, cudaStream_t st, int tx0 = 0, int ntxg = 0);
 // The same over the tiles of all problems of a batch in one launch: `table` is
 // the batch's problem table in device memory (nprob entries, item_base set to
 // the running sum of tile_tc_items), total_items the sum; order_ws holds
 // tile_order_bytes_items(total_items).
 bool launch_tile_tc_batch(const ProblemDev* table, int nprob, int64_t total_items, int* err,
-                          int* tile_ctr, uint32_t* order_ws, int fp16, cudaStream_t st);
+                          int* tile_ctr, uint32_t* order_ws, int form, cudaStream_t st);
 // K0 over all events of a batch: event i belongs to the problem whose ev_base
 // range holds it; keys are offset by the problem's key_base.
 void launch_recentre_batch(const ProblemDev* table, int nprob, int ntotal, float4* ev,

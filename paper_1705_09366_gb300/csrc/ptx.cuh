@@ -1,5 +1,6 @@
-// Inline-PTX wrappers for sm_103a: mbarrier, bulk copy (TMA, non-multicast),
-// tcgen05 (tensor memory allocation, MMA, loads, stores, fences).
+// Inline-PTX wrappers for sm_103a used by the tensor tile kernel: mbarrier,
+// bulk copy (non-multicast), tcgen05 tensor-memory allocation, loads, stores and
+// fences, matrix and instruction descriptors, explicit shared-memory loads.
 #pragma once
 
 #include <stdint.h>
@@ -63,20 +64,6 @@ __device__ __forceinline__ bool mbar_try_wait_ns(uint32_t bar, uint32_t parity, 
     return ok != 0;
 }
 
-// Non-blocking test of the same phase: returns at once (try_wait may suspend
-// the thread for a while when the phase is not complete).
-__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
 // ----------------------------------------------------------- bulk copy ---
 
 // Global -> shared bulk copy completing on an mbarrier (no multicast).
@@ -114,25 +101,6 @@ __device__ __forceinline__ void tc_fence_before() {
 
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// D[tmem] (+)= A[smem] * B[smem]^T, M = 128, kind::f16 (bf16 or fp16 inputs, fp32 accumulate).
-__device__ __forceinline__ void mma_f16_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// Arrives on the mbarrier once every tcgen05 operation issued so far by this
-// thread has completed.
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-        ::"r"(bar) : "memory");
 }
 
 // 32 lanes x 32 columns of 32 bits: lane i of the warp gets row (quarter*32 + i),
@@ -182,9 +150,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
-// Instruction descriptor for kind::f16 with fp32 accumulation, A and B K-major.
-// ab_fmt: 0 = fp16, 1 = bf16.
-__host__ __device__ __forceinline__ uint32_t idesc_f16(uint32_t m, uint32_t n, uint32_t ab_fmt) {
+// Instruction descriptor for kind::f16 / kind::tf32 with fp32 accumulation, A
+// and B K-major.  ab_fmt: 0 = fp16, 1 = bf16 (kind::f16); 2 = tf32 (kind::tf32).
+__host__ __device__ __forceinline__ uint32_t idesc_mma(uint32_t m, uint32_t n, uint32_t ab_fmt) {
     uint32_t d = 0;
     d |= 1u << 4;                 // D format: f32
     d |= (ab_fmt & 7u) << 7;      // A format
@@ -194,85 +162,13 @@ __host__ __device__ __forceinline__ uint32_t idesc_f16(uint32_t m, uint32_t n, u
     return d;
 }
 
-}  // namespace ptx
-}  // namespace stkde
-
-namespace stkde {
-namespace ptx {
-
 // ------------------------------------------------ explicit shared memory ---
-
-__device__ __forceinline__ float4 lds_f4(uint32_t a) {
-    float4 v;
-    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
-    return v;
-}
 
 __device__ __forceinline__ int4 lds_i4(uint32_t a) {
     int4 v;
     asm volatile("ld.shared.v4.s32 {%0,%1,%2,%3}, [%4];"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
     return v;
-}
-
-__device__ __forceinline__ float lds_f(uint32_t a) {
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
-    return v;
-}
-
-__device__ __forceinline__ void sts_f4(uint32_t a, float4 v) {
-    asm volatile("st.shared.v4.f32 [%0], {%1,%2,%3,%4};"
-                 ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
-}
-
-__device__ __forceinline__ void sts_u4(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
-    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};"
-                 ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
-}
-
-__device__ __forceinline__ void sts_i4(uint32_t a, int4 v) {
-    asm volatile("st.shared.v4.s32 [%0], {%1,%2,%3,%4};"
-                 ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
-}
-
-__device__ __forceinline__ void sts_f2(uint32_t a, float2 v) {
-    asm volatile("st.shared.v2.f32 [%0], {%1,%2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
-}
-
-__device__ __forceinline__ void sts_f(uint32_t a, float v) {
-    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
-}
-
-}  // namespace ptx
-}  // namespace stkde
-
-namespace stkde {
-namespace ptx {
-
-// D[tmem] (+)= A[tmem] * B[smem]^T, M = 128, kind::f16.  A occupies 128 lanes x
-// (K/2) columns of tensor memory (two 16-bit values per 32-bit column, the
-// lower K index in the low half).
-__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// Stores 16 consecutive 32-bit columns of this warp's 32 lanes.
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
-        ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
-          "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]),
-          "r"(v[13]), "r"(v[14]), "r"(v[15])
-        : "memory");
 }
 
 }  // namespace ptx

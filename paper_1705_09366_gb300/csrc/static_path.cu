@@ -77,6 +77,12 @@ stkde_status scratch_for_device(int dev, unsigned char** out) {
     return STKDE_OK;
 }
 
+// The tensor tile kernel's form code of an API tensor form.
+int static_tc_form(int form) {
+    return form == STKDE_FORM_TENSOR_FP16X3 ? 1 : form == STKDE_FORM_TENSOR_TF32X3 ? 2
+         : form == STKDE_FORM_TENSOR_TF32X1 ? 3 : 0;
+}
+
 bool is_device_pointer(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -93,7 +99,7 @@ extern "C" stkde_status stkde_compute_static(const double* points, int64_t n,
                                              float* out, int form, int kernel_constants,
                                              void* stream, int sync) {
     if (!out) return STKDE_ERR_INVALID_ARGUMENT;
-    if (form < STKDE_FORM_TENSOR_BF16X3 || form > STKDE_FORM_SCATTER) return STKDE_ERR_INVALID_ARGUMENT;
+    if (form < STKDE_FORM_TENSOR_BF16X3 || form > STKDE_FORM_TENSOR_TF32X1) return STKDE_ERR_INVALID_ARGUMENT;
     if (kernel_constants != STKDE_KERNEL_PRINTED && kernel_constants != STKDE_KERNEL_UNIT_MASS)
         return STKDE_ERR_INVALID_ARGUMENT;
     stkde_status s = check_problem_args(points, n, grid, hs, ht);
@@ -140,8 +146,7 @@ extern "C" stkde_status stkde_compute_static(const double* points, int64_t n,
             Bins b{ev_sorted, start};
             if (form == STKDE_FORM_FP32) {
                 launch_tile_fp32(pl, b, out, err, st);
-            } else if (!launch_tile_tc(pl, b, out, err, tile_ctr, nullptr,
-                                       form == STKDE_FORM_TENSOR_FP16X3 ? 1 : 0, st)) {
+            } else if (!launch_tile_tc(pl, b, out, err, tile_ctr, nullptr, static_tc_form(form), st)) {
                 return STKDE_ERR_UNSUPPORTED;
             }
         }
@@ -156,6 +161,6 @@ extern "C" stkde_status stkde_compute_static(const double* points, int64_t n,
     if (e != cudaSuccess) return STKDE_ERR_CUDA;
     if (h & ERRBIT_NONFINITE) return STKDE_ERR_NONFINITE;
     if (h & ERRBIT_TIMEOUT) return STKDE_ERR_TIMEOUT;
-    if (h & ERRBIT_BOUNDS) return STKDE_ERR_CUDA;
+    if (h & ERRBIT_BOUNDS) return STKDE_ERR_INTERNAL;
     return STKDE_OK;
 }

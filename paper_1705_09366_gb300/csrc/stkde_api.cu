@@ -89,6 +89,18 @@ size_t carve(void* base, int n, uint32_t nkeys, bool host_points, size_t order_b
 
 bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 
+// The tensor tile kernel's form code of an API form (0 bf16x3, 1 fp16x3,
+// 2 tf32x3, 3 tf32x1), or -1 for the forms that do not use it.
+int tc_form(int form) {
+    switch (form) {
+        case STKDE_FORM_TENSOR_BF16X3: return 0;
+        case STKDE_FORM_TENSOR_FP16X3: return 1;
+        case STKDE_FORM_TENSOR_TF32X3: return 2;
+        case STKDE_FORM_TENSOR_TF32X1: return 3;
+        default: return -1;
+    }
+}
+
 stkde_status check_problem(const double* points, int64_t n, const stkde_grid* g, double hs,
                            double ht) {
     if (!g) return STKDE_ERR_INVALID_ARGUMENT;
@@ -223,7 +235,7 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
     if (form == STKDE_FORM_FP32) {
         launch_tile_fp32(pl, b, out, c->d_err, st);
     } else {
-        const int fp16 = form == STKDE_FORM_TENSOR_FP16X3 ? 1 : 0;
+        const int tcf = tc_form(form);
         const size_t row_bytes = sizeof(float) * (size_t)pl.gy * (size_t)pl.gt;  // one X row
         const size_t grid_bytes = row_bytes * (size_t)pl.gx;
         int nslab = 1;
@@ -234,7 +246,7 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
         }
         if (nslab < 2) {
             // heaviest tiles first (two small launches), then the tile kernel
-            if (!launch_tile_tc(pl, b, out, c->d_err, c->d_ctr, w.order, fp16, st))
+            if (!launch_tile_tc(pl, b, out, c->d_err, c->d_ctr, w.order, tcf, st))
                 return STKDE_ERR_UNSUPPORTED;
             c->launches += 2;
         } else {
@@ -243,7 +255,7 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
             int lo[MAX_SLABS + 1];
             for (int k = 0; k <= nslab; ++k) lo[k] = (int)((int64_t)pl.ntx * k / nslab);
             for (int k = 0; k < nslab; ++k) {
-                if (!launch_tile_tc(pl, b, out, c->d_err, c->d_ctr, w.order, fp16, st, lo[k],
+                if (!launch_tile_tc(pl, b, out, c->d_err, c->d_ctr, w.order, tcf, st, lo[k],
                                     lo[k + 1] - lo[k]))
                     return STKDE_ERR_UNSUPPORTED;
                 cudaEventRecord(c->slab_ev[k], st);
@@ -356,6 +368,7 @@ const char* stkde_status_string(stkde_status s) {
         case STKDE_ERR_TIMEOUT: return "device-side wait timed out";
         case STKDE_ERR_UNSUPPORTED: return "unsupported device or form";
         case STKDE_ERR_NONFINITE: return "non-finite event coordinate";
+        case STKDE_ERR_INTERNAL: return "device-side consistency check failed";
     }
     return "unknown status";
 }
@@ -365,7 +378,7 @@ stkde_status stkde_create(stkde_ctx** out, const stkde_options* opt) {
     *out = nullptr;
     stkde_options o;
     if (opt) o = *opt; else stkde_default_options(&o);
-    if (o.form < STKDE_FORM_TENSOR_BF16X3 || o.form > STKDE_FORM_SCATTER)
+    if (o.form < STKDE_FORM_TENSOR_BF16X3 || o.form > STKDE_FORM_TENSOR_TF32X1)
         return STKDE_ERR_INVALID_ARGUMENT;
     if (o.kernel_constants != STKDE_KERNEL_PRINTED && o.kernel_constants != STKDE_KERNEL_UNIT_MASS)
         return STKDE_ERR_INVALID_ARGUMENT;
@@ -443,7 +456,7 @@ stkde_status stkde_synchronize(stkde_ctx* c) {
     if (h) cudaMemset(c->d_err, 0, sizeof(int));
     if (h & ERRBIT_NONFINITE) return STKDE_ERR_NONFINITE;
     if (h & ERRBIT_TIMEOUT) return STKDE_ERR_TIMEOUT;
-    if (h & ERRBIT_BOUNDS) return STKDE_ERR_CUDA;
+    if (h & ERRBIT_BOUNDS) return STKDE_ERR_INTERNAL;
     return STKDE_OK;
 }
 
@@ -484,7 +497,7 @@ stkde_status stkde_compute(stkde_ctx* c, const double* points, int64_t n, const 
         if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
         const Plan pl = make_plan(c->opt.kernel_constants, n, g, hs, ht, c->opt.slab);
         Workspace w;
-        const bool tensor = c->opt.form == STKDE_FORM_TENSOR_BF16X3 || c->opt.form == STKDE_FORM_TENSOR_FP16X3;
+        const bool tensor = tc_form(c->opt.form) >= 0;
         const size_t order_bytes = tensor ? tile_order_bytes(pl) : 0;
         const size_t need = carve(nullptr, (int)n, pl.nkeys, pkind == 0, order_bytes, nullptr);
         s = ensure_ws(c, need);
@@ -520,7 +533,9 @@ stkde_status stkde_compute_adaptive(stkde_ctx* c, const double* points, int64_t 
     // grid and event checks (the bandwidths are checked below)
     stkde_status s = check_problem(points, n, g, g->sres, g->tres);
     if (s != STKDE_OK) return s;
-    if (c->opt.form == STKDE_FORM_SCATTER) return STKDE_ERR_UNSUPPORTED;
+    if (c->opt.form == STKDE_FORM_SCATTER || c->opt.form == STKDE_FORM_TENSOR_TF32X3 ||
+        c->opt.form == STKDE_FORM_TENSOR_TF32X1)
+        return STKDE_ERR_UNSUPPORTED;
     if (n == 0) return stkde_compute(c, points, 0, g, g->sres, g->tres, out);
     if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
     const int okind = pointer_kind(out, c->device);
@@ -672,7 +687,7 @@ stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int c
     if (count == 0) return STKDE_OK;
     const int form = c->opt.form;
     if (form == STKDE_FORM_SCATTER) return STKDE_ERR_UNSUPPORTED;
-    const bool tensor = form == STKDE_FORM_TENSOR_BF16X3 || form == STKDE_FORM_TENSOR_FP16X3;
+    const bool tensor = tc_form(form) >= 0;
     if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
 
     // validate everything and lay the batch out before any launch
@@ -783,8 +798,7 @@ stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int c
     c->launches += ntot > 0 ? 2 : 1;
     mark(c);
     if (tensor) {
-        if (!launch_tile_tc_batch(dtab, count, itot, c->d_err, c->d_ctr, order,
-                                  form == STKDE_FORM_TENSOR_FP16X3 ? 1 : 0, st))
+        if (!launch_tile_tc_batch(dtab, count, itot, c->d_err, c->d_ctr, order, tc_form(form), st))
             return STKDE_ERR_UNSUPPORTED;
         c->launches += itot > 0 ? 3 : 0;
     } else {

@@ -78,6 +78,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <atomic>
+
 namespace stkde {
 
 namespace {
@@ -91,18 +93,29 @@ constexpr int NTHREADS = 16 * 32;
 constexpr int PAGE = 256;          // events per staging page (128 with per-event bandwidths)
 constexpr uint32_t PAGE_BYTES = PAGE * 16;
 constexpr int NPAGES = 5;          // pages per stream
-constexpr int CHUNK = 16;          // events per MMA (K of kind::f16)
-constexpr int MAXCH = PAGE / CHUNK;
-constexpr int MAXENT = 64;         // entries per page: 16 chunks x at most 4 windows
+constexpr int MAXCH = PAGE / 8;    // chunk records per page (8-event chunks of the tf32 forms)
+constexpr int MAXENT = 128;        // entries per page: chunks x their column windows
 constexpr int NCAP = 80;           // T columns per entry (one column window)
 constexpr int NSTAGE = 6;          // stages per stream, handed over one at a time
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr uint64_t DRAIN_NS = 200000000ull;
-constexpr uint32_t A_BYTES = TILE_XY * CHUNK * 2;   // 4 KB
-constexpr uint32_t B_BYTES = NCAP * CHUNK * 2;      // 2.5 KB
+constexpr uint32_t A_BYTES = TILE_XY * 32;          // one A part: 128 rows x 32 bytes (4 KB)
+constexpr uint32_t B_BYTES = NCAP * 32;             // one B part: NCAP rows x 32 bytes (2.5 KB)
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr uint32_t CORE_LBO = 128;  // next core matrix along K
 constexpr uint32_t CORE_SBO = 256;  // next core matrix along M / N
+enum { FORM_BF16X3 = 0, FORM_FP16X3 = 1, FORM_TF32X3 = 2, FORM_TF32X1 = 3 };
+
+// A chunk is the K of one MMA: 16 events of 16-bit parts (kind::f16) or 8 events
+// of 32-bit parts (kind::tf32); either way a row of one A or B part is 32 bytes.
+template <int FORM>
+struct Cfg {
+    static constexpr bool TF32 = FORM >= FORM_TF32X3;
+    static constexpr bool FP16 = FORM == FORM_FP16X3;
+    static constexpr int CHUNK = TF32 ? 8 : 16;
+    static constexpr uint32_t ABFMT = TF32 ? 2u : FP16 ? 0u : 1u;
+};
+
 // per-generator factor tables (rows padded so the A loop's reads hit distinct banks)
 constexpr int XA_STRIDE = 20;       // floats per x row: 1 - u^2 for 16 events
 constexpr int YB_STRIDE = 36;       // floats per y row: 1 - v^2, then v^2, for 16 events
@@ -203,19 +216,56 @@ __device__ __forceinline__ void split_rn(float2 v, uint32_t& hi, uint32_t& lo) {
     }
 }
 
-// The three products of one entry, issued by one elected lane of a converged warp:
-// D += Ahi*Bhi, D += Ahi*Blo, D += Alo*Bhi.
+// hi = the value with its low 13 significand bits cleared (exact in tf32), lo =
+// the remainder (exact in fp32), for a pair v; elements whose disk-test
+// difference d is negative (or -0) give 0.
+__device__ __forceinline__ void split_tf32(float2 v, float2 d, uint32_t& h0, uint32_t& h1, uint32_t& l0,
+                                           uint32_t& l1) {
+    const uint32_t m0 = (uint32_t)(__float_as_int(d.x) >> 31), m1 = (uint32_t)(__float_as_int(d.y) >> 31);
+    const uint32_t a0 = __float_as_uint(v.x) & ~m0, a1 = __float_as_uint(v.y) & ~m1;
+    h0 = a0 & 0xffffe000u;
+    h1 = a1 & 0xffffe000u;
+    const float2 r = __fadd2_rn(make_float2(__uint_as_float(a0), __uint_as_float(a1)),
+                                make_float2(-__uint_as_float(h0), -__uint_as_float(h1)));
+    l0 = __float_as_uint(r.x);
+    l1 = __float_as_uint(r.y);
+}
+
+// The products of one entry, issued by one elected lane of a converged warp:
+// D += Ahi*Bhi, D += Ahi*Blo, D += Alo*Bhi (kind::f16 or kind::tf32), or only
+// D += Ahi*Bhi for the one-product form.
+template <int FORM>
 __device__ __forceinline__ void mma3_elect(uint32_t d, uint64_t ahi, uint64_t alo, uint64_t bhi,
                                            uint64_t blo, uint32_t idesc) {
-    asm volatile(
-        "{\n\t.reg .pred e, acc;\n\t"
-        "setp.ne.b32 acc, 1, 0;\n\t"
-        "elect.sync _|e, 0xffffffff;\n\t"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %3, %5, acc;\n\t"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %4, %5, acc;\n\t"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %5, acc;\n\t}"
-        ::"r"(d), "l"(ahi), "l"(alo), "l"(bhi), "l"(blo), "r"(idesc)
-        : "memory");
+    if constexpr (FORM == FORM_TF32X1) {
+        asm volatile(
+            "{\n\t.reg .pred e, acc;\n\t"
+            "setp.ne.b32 acc, 1, 0;\n\t"
+            "elect.sync _|e, 0xffffffff;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, acc;\n\t}"
+            ::"r"(d), "l"(ahi), "l"(bhi), "r"(idesc)
+            : "memory");
+    } else if constexpr (FORM == FORM_TF32X3) {
+        asm volatile(
+            "{\n\t.reg .pred e, acc;\n\t"
+            "setp.ne.b32 acc, 1, 0;\n\t"
+            "elect.sync _|e, 0xffffffff;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %3, %5, acc;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %4, %5, acc;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], %2, %3, %5, acc;\n\t}"
+            ::"r"(d), "l"(ahi), "l"(alo), "l"(bhi), "l"(blo), "r"(idesc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred e, acc;\n\t"
+            "setp.ne.b32 acc, 1, 0;\n\t"
+            "elect.sync _|e, 0xffffffff;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %3, %5, acc;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %4, %5, acc;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %5, acc;\n\t}"
+            ::"r"(d), "l"(ahi), "l"(alo), "l"(bhi), "l"(blo), "r"(idesc)
+            : "memory");
+    }
 }
 
 // tcgen05.commit by one elected lane of a converged warp.
@@ -297,11 +347,14 @@ __device__ __forceinline__ ProblemDev fetch_problem(const ProblemDev& single,
     return table ? table[p] : single;
 }
 
-template <bool FP16, bool ADAPT>
+template <int FORM, bool ADAPT>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
           int* __restrict__ err, int* __restrict__ tile_ctr, const uint32_t* __restrict__ order,
           int64_t nitems, int flush_chunks) {
+    using C = Cfg<FORM>;
+    constexpr int CHUNK = C::CHUNK;
+    constexpr bool FP16 = C::FP16;
     extern __shared__ __align__(1024) uint8_t smem[];
     const uint32_t sb = ptx::smem_addr(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -558,7 +611,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
         float* yb = reinterpret_cast<float*>(tab + TAB_YB);
         float* tkt = reinterpret_cast<float*>(tab + TAB_TK);
         float* tih = tkt + CHUNK;  // per-event 1/htv_i (ADAPT)
-        const uint32_t fmt = FP16 ? 0u : 1u;
+        const uint32_t fmt = C::ABFMT;
         bool ok = true;
         uint32_t ebase = 0;  // the stream's entries before the current page
         uint32_t emod = 0;   // ebase mod NGEN
@@ -577,7 +630,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             if (lane == 0) {
                 uint32_t idesc = 0, mask = 0, inc_lo = 0, inc_hi = 0;
                 if (flags & F_MMA) {
-                    idesc = ptx::idesc_f16(128, (uint32_t)ncols, fmt);
+                    idesc = ptx::idesc_mma(128, (uint32_t)ncols, fmt);
                     const uint32_t b0 = (uint32_t)c0 >> 5, b1 = (uint32_t)(c0 + ncols - 1) >> 5;
                     mask = ((2u << b1) - 1u) & ~((1u << b0) - 1u);
                     inc_lo = ((mask & 15u) * 0x204081u) & 0x01010101u;
@@ -633,9 +686,10 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 const int c0 = cinfo.x & 0xffff, cend = cinfo.x >> 16;
                 const int count = min(CHUNK, kept - ch * CHUNK);
 
-                // factor tables of K_s for the chunk's 16 events (missing events
-                // get u, v >= 2: negative factors, masked below)
-                const int k = lane & 15, half = lane >> 4;
+                // factor tables of K_s for the chunk's events (missing events get
+                // u, v >= 2: negative factors, masked below); lane = (part, event)
+                constexpr int NPART = 32 / CHUNK;
+                const int k = lane % CHUNK, half = lane / CHUNK;
                 const bool real = k < count;
                 float4 ek = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (real) ek = page[ch * CHUNK + k];
@@ -653,15 +707,15 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 const float cu = real ? ((float)X0 + 0.5f - ek.x) * ihs : 2.0f;
                 const float cv = real ? ((float)Y0 + 0.5f - ek.y) * ihs : 2.0f;
 #pragma unroll
-                for (int i = 0; i < TX / 2; ++i) {
-                    const int x = half + 2 * i;
+                for (int i = 0; i < TX / NPART; ++i) {
+                    const int x = half + NPART * i;
                     const float u = fmaf((float)x, ihs, cu);
                     if constexpr (ADAPT) xa[x * XA_STRIDE + k] = wk * fmaf(-u, u, 1.0f);
                     else xa[x * XA_STRIDE + k] = fmaf(-u, u, 1.0f);
                 }
 #pragma unroll
-                for (int i = 0; i < TY / 2; ++i) {
-                    const int y = half + 2 * i;
+                for (int i = 0; i < TY / NPART; ++i) {
+                    const int y = half + NPART * i;
                     const float v = fmaf((float)y, ihs, cv);
                     const float vv = v * v;
                     yb[y * YB_STRIDE + k] = 1.0f - vv;
@@ -682,11 +736,14 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 // A = K_s without c_s: row r = voxel (x = r / 8, y = r % 8); lane
                 // owns rows lane + 32 j, all with y = lane % 8.  The disk test
                 // (u^2 + v^2 < 1, i.e. (1 - u^2) - v^2 > 0) masks both halves.
+                // A row holds CHUNK events in 32 bytes: 16-bit parts packed in
+                // pairs (kind::f16) or one 32-bit part per event (kind::tf32).
                 {
+                    constexpr int PP = CHUNK / 2;  // event pairs per row
                     const float* yrow = yb + (lane & 7) * YB_STRIDE;
-                    float2 bq[8], vq[8];
+                    float2 bq[PP], vq[PP];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < PP / 2; ++i) {
                         const float4 tb4 = *reinterpret_cast<const float4*>(yrow + 4 * i);
                         const float4 tv4 = *reinterpret_cast<const float4*>(yrow + 16 + 4 * i);
                         bq[2 * i] = make_float2(tb4.x, tb4.y);
@@ -699,7 +756,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                         const float* xrow = xa + ((lane >> 3) + 4 * jj) * XA_STRIDE;
                         uint32_t ah[8], al[8];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
+                        for (int i = 0; i < PP / 2; ++i) {
                             const float4 t4 = *reinterpret_cast<const float4*>(xrow + 4 * i);
                             const float2 aq[2] = {make_float2(t4.x, t4.y), make_float2(t4.z, t4.w)};
 #pragma unroll
@@ -707,10 +764,14 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                                 const int pp = 2 * i + h;
                                 const float2 pr = __fmul2_rn(aq[h], bq[pp]);
                                 const float2 d = __fadd2_rn(aq[h], fneg2(vq[pp]));
-                                split_rn<FP16>(pr, ah[pp], al[pp]);
-                                const uint32_t m = sign_mask2(d.x, d.y);
-                                ah[pp] &= ~m;
-                                al[pp] &= ~m;
+                                if constexpr (C::TF32) {
+                                    split_tf32(pr, d, ah[2 * pp], ah[2 * pp + 1], al[2 * pp], al[2 * pp + 1]);
+                                } else {
+                                    split_rn<FP16>(pr, ah[pp], al[pp]);
+                                    const uint32_t m = sign_mask2(d.x, d.y);
+                                    ah[pp] &= ~m;
+                                    al[pp] &= ~m;
+                                }
                             }
                         }
                         const int r = lane + 32 * jj;
@@ -724,15 +785,16 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 }
                 // B = K_t without c_t: (1 - w^2)_+ for the window's columns
                 {
-                    const int hh = lane & 1;  // events 8 hh .. 8 hh + 7
-                    float2 tq[4], iq[4];
+                    constexpr int EH = CHUNK / 2;   // events of one core-matrix row (16 bytes)
+                    const int hh = lane & 1;        // events EH hh .. EH hh + EH - 1
+                    float2 tq[EH / 2], iq[EH / 2];
 #pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const float4 t4 = *reinterpret_cast<const float4*>(tkt + 8 * hh + 4 * i);
+                    for (int i = 0; i < EH / 4; ++i) {
+                        const float4 t4 = *reinterpret_cast<const float4*>(tkt + EH * hh + 4 * i);
                         tq[2 * i] = make_float2(-t4.x, -t4.y);
                         tq[2 * i + 1] = make_float2(-t4.z, -t4.w);
                         if constexpr (ADAPT) {
-                            const float4 i4 = *reinterpret_cast<const float4*>(tih + 8 * hh + 4 * i);
+                            const float4 i4 = *reinterpret_cast<const float4*>(tih + EH * hh + 4 * i);
                             iq[2 * i] = make_float2(i4.x, i4.y);
                             iq[2 * i + 1] = make_float2(i4.z, i4.w);
                         }
@@ -745,10 +807,12 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                         const float2 n2 = make_float2((float)n, (float)n);
                         uint32_t h[4], l[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
+                        for (int i = 0; i < EH / 2; ++i) {
                             const float2 wv = __fmul2_rn(__fadd2_rn(n2, tq[i]), ADAPT ? iq[i] : ih2);
                             const float2 kt = __ffma2_rn(fneg2(wv), wv, one2);
-                            split_rn<FP16>(make_float2(fmaxf(kt.x, 0.0f), fmaxf(kt.y, 0.0f)), h[i], l[i]);
+                            const float2 kp = make_float2(fmaxf(kt.x, 0.0f), fmaxf(kt.y, 0.0f));
+                            if constexpr (C::TF32) split_tf32(kp, kp, h[2 * i], h[2 * i + 1], l[2 * i], l[2 * i + 1]);
+                            else split_rn<FP16>(kp, h[i], l[i]);
                         }
                         const uint32_t off = (uint32_t)(n >> 3) * CORE_SBO + (uint32_t)(n & 7) * 16 + hh * CORE_LBO;
                         *reinterpret_cast<uint4*>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -855,7 +919,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                     cnt_hi += inc_hi;
                     touched |= (uint32_t)h0.w;
                     const uint64_t so = (uint64_t)s * (STAGE_BYTES >> 4);
-                    mma3_elect(acc + (uint32_t)c0, d_ahi + so, d_alo + so, d_bhi + so, d_blo + so, idesc);
+                    mma3_elect<FORM>(acc + (uint32_t)c0, d_ahi + so, d_alo + so, d_bhi + so, d_blo + so, idesc);
                 }
             }
             if (flags & F_ITEM_END) {
@@ -1019,21 +1083,23 @@ __global__ void k_tile_order(int nitems, const uint32_t* __restrict__ cost,
     order[base + atomicAdd(&cursor[b], 1u)] = (uint32_t)i;
 }
 
-template <bool FP16, bool ADAPT>
+template <int FORM, bool ADAPT>
 bool launch_cfg(const ProblemDev& single, const ProblemDev* table, int nprob, int64_t items,
                 int* err, int* tile_ctr, uint32_t* order_ws, cudaStream_t st) {
-    auto kern = k_tile_tc<FP16, ADAPT>;
+    auto kern = k_tile_tc<FORM, ADAPT>;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     // the shared-memory limit is raised once per device this process uses
+    // (a function attribute per device and form; setting it again is harmless,
+    // so host threads that race here at worst set it twice)
     constexpr int MAXDEV = 64;
-    static bool attr[MAXDEV] = {};
+    static std::atomic<bool> attr[MAXDEV];
     if (dev < 0 || dev >= MAXDEV) return false;
-    if (!attr[dev]) {
+    if (!attr[dev].load(std::memory_order_acquire)) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::TOTAL) !=
             cudaSuccess)
             return false;
-        attr[dev] = true;
+        attr[dev].store(true, std::memory_order_release);
     }
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (items <= 0) return true;
@@ -1052,10 +1118,12 @@ bool launch_cfg(const ProblemDev& single, const ProblemDev* table, int nprob, in
         k_tile_order<<<blocks, 256, 0, st>>>((int)items, cost, hist, cursor, ord);
         order = ord;
     }
-    // chunks (three accumulation steps each) per 32-column block at which the
-    // block is drained (a power of two: the MMA warp tests it as a bit mask):
-    // bounds the round-toward-zero drift of the tensor-core accumulation per drain
-    const int flush_chunks = FP16 ? 64 : 128;
+    // chunks (K steps, three accumulation steps each) per 32-column block at
+    // which the block is drained (a power of two: the MMA warp tests it as a bit
+    // mask): bounds the round-toward-zero drift of the tensor-core accumulation
+    // per drain.  kind::tf32 takes twice the K steps per event and drifts more
+    // per step.
+    const int flush_chunks = FORM == FORM_FP16X3 ? 64 : FORM == FORM_TF32X3 ? 32 : 128;
     kern<<<grid, NTHREADS, L::TOTAL, st>>>(single, table, nprob, err, tile_ctr, order, items,
                                            flush_chunks);
     return true;
@@ -1073,8 +1141,30 @@ size_t tile_order_bytes_items(int64_t items) {
 
 size_t tile_order_bytes(const Plan& pl) { return tile_order_bytes_items(tile_tc_items(pl)); }
 
+// The kernel of form `form` (0 bf16x3, 1 fp16x3, 2 tf32x3, 3 tf32x1; per-event
+// bandwidths with the 16-bit forms only).
+template <bool ADAPT>
+bool launch_form(int form, const ProblemDev& single, const ProblemDev* table, int nprob, int64_t items,
+                 int* err, int* tile_ctr, uint32_t* order_ws, cudaStream_t st) {
+    switch (form) {
+        case FORM_BF16X3:
+            return launch_cfg<FORM_BF16X3, ADAPT>(single, table, nprob, items, err, tile_ctr, order_ws, st);
+        case FORM_FP16X3:
+            return launch_cfg<FORM_FP16X3, ADAPT>(single, table, nprob, items, err, tile_ctr, order_ws, st);
+        default:
+            break;
+    }
+    if constexpr (!ADAPT) {
+        if (form == FORM_TF32X3)
+            return launch_cfg<FORM_TF32X3, false>(single, table, nprob, items, err, tile_ctr, order_ws, st);
+        if (form == FORM_TF32X1)
+            return launch_cfg<FORM_TF32X1, false>(single, table, nprob, items, err, tile_ctr, order_ws, st);
+    }
+    return false;
+}
+
 bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* tile_ctr,
-                    uint32_t* order_ws, int fp16, cudaStream_t st, int tx0, int ntxg) {
+                    uint32_t* order_ws, int form, cudaStream_t st, int tx0, int ntxg) {
     ProblemDev single{};
     single.pl = pl;
     single.ev = b.ev;
@@ -1085,19 +1175,15 @@ bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* ti
     single.tx0 = tx0;
     single.ntxg = ntxg;
     const int64_t items = ntxg > 0 ? tile_tc_items(pl) / pl.ntx * ntxg : tile_tc_items(pl);
-    if (b.evp)
-        return fp16 ? launch_cfg<true, true>(single, nullptr, 1, items, err, tile_ctr, order_ws, st)
-                    : launch_cfg<false, true>(single, nullptr, 1, items, err, tile_ctr, order_ws, st);
-    return fp16 ? launch_cfg<true, false>(single, nullptr, 1, items, err, tile_ctr, order_ws, st)
-                : launch_cfg<false, false>(single, nullptr, 1, items, err, tile_ctr, order_ws, st);
+    if (b.evp) return launch_form<true>(form, single, nullptr, 1, items, err, tile_ctr, order_ws, st);
+    return launch_form<false>(form, single, nullptr, 1, items, err, tile_ctr, order_ws, st);
 }
 
 bool launch_tile_tc_batch(const ProblemDev* table, int nprob, int64_t total_items, int* err,
-                          int* tile_ctr, uint32_t* order_ws, int fp16, cudaStream_t st) {
+                          int* tile_ctr, uint32_t* order_ws, int form, cudaStream_t st) {
     if (nprob <= 0) return true;
     const ProblemDev none{};
-    return fp16 ? launch_cfg<true, false>(none, table, nprob, total_items, err, tile_ctr, order_ws, st)
-                : launch_cfg<false, false>(none, table, nprob, total_items, err, tile_ctr, order_ws, st);
+    return launch_form<false>(form, none, table, nprob, total_items, err, tile_ctr, order_ws, st);
 }
 
 }  // namespace stkde

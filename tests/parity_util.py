@@ -5,7 +5,10 @@ import numpy as np
 
 # Gates from the accuracy targets: max |gpu - oracle| / max(oracle), after the
 # binary32 tie slack of the oracle (pairs on the cylinder wall may go either way).
-TOL = {"fp32": 1e-5, "bf16x3": 2e-5, "fp16x3": 1e-5, "scatter": 1e-5}
+TOL = {"fp32": 1e-5, "bf16x3": 2e-5, "fp16x3": 1e-5, "scatter": 1e-5, "tf32x3": 1e-5}
+# the one-product tf32 form is reported, not gated: about 2^-11 per term; this
+# bound only catches a broken kernel
+REPORT_ONLY_BOUND = {"tf32x1": 2e-3}
 
 
 def excess_error(got, ref, slack, scale=None):

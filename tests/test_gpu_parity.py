@@ -5,7 +5,8 @@ Element by element on the same seeded inputs: the full grid for the small
 densest, corners, edges, random) of the large 1024x1024x512 workload in the
 launch configuration the benchmark times.  Gates: max |gpu - oracle| over the
 grid maximum, after the oracle's binary32 tie slack, <= 1e-5 (fp32, fp16x3,
-scatter) and <= 2e-5 (bf16x3).
+tf32x3, scatter) and <= 2e-5 (bf16x3); the one-product tf32x1 form is reported
+against a loose bound only.
 """
 import zlib
 
@@ -20,7 +21,7 @@ from paper_1705_09366_gb300 import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TILE_FORMS = ["bf16x3", "fp16x3", "fp32"]
+TILE_FORMS = ["bf16x3", "fp16x3", "tf32x3", "fp32"]
 ALL_FORMS = TILE_FORMS + ["scatter"]
 
 
@@ -69,6 +70,17 @@ def test_medium_full_grid(form):
     assert np.isfinite(got).all()
     err = pu.excess_error(got, ref, slack)
     assert err <= pu.TOL[form], err
+
+
+@pytest.mark.parametrize("name", ["small", "medium"])
+def test_tf32x1_reported(name):
+    w = getattr(synth, name)()
+    ref, slack = oracle_full(w)
+    got = run("tf32x1", w).cpu().numpy()
+    assert np.isfinite(got).all()
+    err = pu.excess_error(got, ref, slack)
+    print(f"tf32x1 {name}: max error {err:.3e} of the grid maximum (reported, not gated)")
+    assert err <= pu.REPORT_ONLY_BOUND["tf32x1"], err
 
 
 @pytest.fixture(scope="module")
