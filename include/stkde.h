@@ -32,7 +32,14 @@
  *    Errors found on the device (non-finite coordinates, a bounded wait that
  *    gave up) are latched and returned by stkde_synchronize, or by the next
  *    call that synchronizes.
- *  - A context is not thread-safe: use one per host thread.
+ *  - A context is not thread-safe: use one per host thread.  Contexts share
+ *    no device state, so several contexts on several streams run concurrently.
+ *  - Stream capture (CUDA graphs): stkde_compute and stkde_compute_batch may be
+ *    captured when their events and outputs are device memory and the
+ *    workspace already fits (an earlier call of the same size, or
+ *    stkde_reserve); a call that would have to grow a buffer, wait for the
+ *    stream or copy host memory returns STKDE_ERR_UNSUPPORTED before enqueueing
+ *    anything, and so do the synchronous and per-event-bandwidth entry points.
  */
 #ifndef STKDE_H
 #define STKDE_H
@@ -145,9 +152,11 @@ typedef struct {
 /* Computes `count` independent problems in one batched call (the paper's
  * runs are one problem each; batching is this library's addition for many small
  * problems): one re-centre, one binning sort and one bin-bounds pass over the
- * concatenated events of all problems, then, for the tensor forms, one
- * persistent tile-kernel launch whose work queue holds the tiles of every
- * problem, heaviest first (the fp32 form launches its tile kernel per problem).
+ * concatenated events of all problems, then one tile-kernel launch over the
+ * tiles of every problem (the tensor forms: a persistent kernel whose work
+ * queue holds them heaviest first; the fp32 form: one block per tile).  The
+ * problem table travels in kernel parameters, so the call keeps no pointer to
+ * `problems` after it returns.
  * Each result is bit-identical to the problem computed alone by stkde_compute
  * with the same form.  Events may be host or device memory per problem; outputs
  * must be device memory of the context's device.  Errors: INVALID_ARGUMENT (any
@@ -237,10 +246,13 @@ STKDE_API int stkde_last_launch_count(stkde_ctx* ctx);
  * (cudaStream_t, NULL = legacy default stream), `form` and `kernel_constants`
  * are as in stkde_options.  All scratch lives in one fixed file-scope device
  * array of about 16 MB that every device loading the library keeps until the
- * process exits; its device address is looked up once per device on the first
- * call made with that device current, so make that first call before any
- * stream capture.  All calls on a device share that array: calls whose work
- * overlaps on the GPU race and must be serialised by the caller.
+ * process exits; its device address is looked up on every call made outside
+ * stream capture, and a call made while `stream` is being captured uses the
+ * address the last call on that device found, so make a first call on each
+ * device before any capture (a captured call with no such predecessor, or with
+ * sync != 0, returns STKDE_ERR_UNSUPPORTED).  All calls on a device share that
+ * array: calls whose work overlaps on the GPU race and must be serialised by
+ * the caller.
  * Returns STKDE_ERR_UNSUPPORTED, before any launch, when n exceeds
  * STKDE_STATIC_MAX_EVENTS or the grid needs more than STKDE_STATIC_MAX_BINS bin
  * boundaries; INVALID_ARGUMENT for host pointers or the argument errors of
@@ -251,6 +263,17 @@ STKDE_API stkde_status stkde_compute_static(const double* points, int64_t n,
                                             const stkde_grid* grid, double hs, double ht,
                                             float* out, int form, int kernel_constants,
                                             void* stream, int sync);
+
+/* Grows the context's workspace to at least `bytes` now (waiting for the stream
+ * if it must grow), so that later calls whose workspace fits allocate nothing:
+ * a serving loop then never takes the device-wide synchronisation of
+ * cudaMalloc/cudaFree, and the calls can be captured into a CUDA graph.  A
+ * problem of n events needs about 56 n bytes plus 4 bytes per 512 voxels of
+ * grid (more with host events or per-event bandwidths).  The workspace never
+ * shrinks before stkde_destroy.  Errors: INVALID_ARGUMENT (NULL ctx), OOM (the
+ * workspace is then empty; the context stays usable), UNSUPPORTED (during
+ * stream capture). */
+STKDE_API stkde_status stkde_reserve(stkde_ctx* ctx, size_t bytes);
 
 /* Frees the context and its workspace (waits for its stream first). */
 STKDE_API void stkde_destroy(stkde_ctx* ctx);

@@ -13,13 +13,16 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 
 __all__ = [
     "Options", "Grid", "Problem", "StkdeError", "Context", "lib", "lib_path",
     "stkde_default_options", "stkde_create", "stkde_compute", "stkde_compute_batch",
     "stkde_count_updates", "stkde_synchronize", "stkde_phase_times", "stkde_destroy",
-    "stkde_status_string", "stkde_last_launch_count", "stkde_compute_static", "FORM_TENSOR_BF16X3",
-    "FORM_TENSOR_FP16X3", "FORM_FP32", "FORM_SCATTER", "FORM_TENSOR_TF32X3", "FORM_TENSOR_TF32X1", "KERNEL_PRINTED", "KERNEL_UNIT_MASS", "EXPORTED_SYMBOLS",
+    "stkde_status_string", "stkde_last_launch_count", "stkde_compute_static", "stkde_reserve",
+    "stkde_inject_fault", "FORM_TENSOR_BF16X3", "FORM_TENSOR_FP16X3", "FORM_FP32", "FORM_SCATTER",
+    "FORM_TENSOR_TF32X3", "FORM_TENSOR_TF32X1", "KERNEL_PRINTED", "KERNEL_UNIT_MASS",
+    "FAULT_NONE", "FAULT_ALLOC", "FAULT_WITHHOLD_PAGE", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -46,11 +49,17 @@ FORMS = {"bf16x3": FORM_TENSOR_BF16X3, "fp16x3": FORM_TENSOR_FP16X3, "fp32": FOR
 KERNEL_PRINTED = 0
 KERNEL_UNIT_MASS = 1
 
+# fault injection (include/stkde_testing.h)
+FAULT_NONE = 0
+FAULT_ALLOC = 1
+FAULT_WITHHOLD_PAGE = 2
+
 EXPORTED_SYMBOLS = (
     "stkde_default_options", "stkde_create", "stkde_compute", "stkde_compute_batch",
     "stkde_count_updates", "stkde_synchronize", "stkde_phase_times", "stkde_destroy",
     "stkde_status_string", "stkde_last_launch_count", "stkde_compute_static",
     "stkde_compute_adaptive", "stkde_count_updates_adaptive", "stkde_abramson_bandwidths",
+    "stkde_reserve", "stkde_inject_fault",
 )
 
 STATIC_MAX_EVENTS = 262144
@@ -118,6 +127,10 @@ def lib():
         l.stkde_compute_static.argtypes = [vp, i64, ctypes.POINTER(Grid), dbl, dbl, vp, ctypes.c_int,
                                            ctypes.c_int, vp, ctypes.c_int]
         l.stkde_compute_static.restype = ctypes.c_int
+        l.stkde_reserve.argtypes = [vp, ctypes.c_size_t]
+        l.stkde_reserve.restype = ctypes.c_int
+        l.stkde_inject_fault.argtypes = [vp, ctypes.c_int, i64]
+        l.stkde_inject_fault.restype = ctypes.c_int
         l.stkde_last_launch_count.argtypes = [vp]
         l.stkde_last_launch_count.restype = ctypes.c_int
         l.stkde_destroy.argtypes = [vp]
@@ -145,8 +158,14 @@ def _ptr(buf) -> int:
     raise TypeError(f"unsupported buffer type {type(buf)!r}")
 
 
-def _stream_handle(stream) -> int:
+def _stream_handle(stream, device=None) -> int:
+    """cudaStream_t of ``stream``: an int handle, an object with ``cuda_stream``
+    (torch.cuda.Stream), or None = torch's current stream (of ``device``) when
+    torch is imported and sees a GPU, else the legacy default stream (0)."""
     if stream is None:
+        t = sys.modules.get("torch")
+        if t is not None and t.cuda.is_available():
+            return int(t.cuda.current_stream(device).cuda_stream)
         return 0
     if isinstance(stream, int):
         return stream
@@ -172,7 +191,7 @@ def stkde_create(device: int = 0, stream=None, form="bf16x3", kernel_constants: 
                  t_block: int = 0, slab: int = 0, profile: bool = False) -> ctypes.c_void_p:
     o = stkde_default_options()
     o.device = int(device)
-    o.stream = _stream_handle(stream)
+    o.stream = _stream_handle(stream, int(device))
     o.form = FORMS[form] if isinstance(form, str) else int(form)
     o.kernel_constants = int(kernel_constants)
     o.t_block = int(t_block)
@@ -245,6 +264,15 @@ def stkde_compute_static(points, n: int, grid: Grid, hs: float, ht: float, out, 
     _check(lib().stkde_compute_static(_ptr(points), int(n), ctypes.byref(grid), float(hs), float(ht),
                                       _ptr(out), f, int(kernel_constants), _stream_handle(stream),
                                       int(bool(sync))), "stkde_compute_static")
+
+
+def stkde_reserve(ctx, nbytes: int) -> None:
+    _check(lib().stkde_reserve(ctx, int(nbytes)), "stkde_reserve")
+
+
+def stkde_inject_fault(ctx, fault: int, arg: int = 0) -> None:
+    """Test hook (include/stkde_testing.h): arms one injected failure on ctx."""
+    _check(lib().stkde_inject_fault(ctx, int(fault), int(arg)), "stkde_inject_fault")
 
 
 def stkde_last_launch_count(ctx) -> int:
@@ -355,3 +383,10 @@ class Context:
 
     def last_launch_count(self):
         return stkde_last_launch_count(self.handle)
+
+    def reserve(self, nbytes: int):
+        """Grows the workspace now (see stkde_reserve)."""
+        stkde_reserve(self.handle, nbytes)
+
+    def inject_fault(self, fault: int, arg: int = 0):
+        stkde_inject_fault(self.handle, fault, arg)

@@ -43,7 +43,8 @@ def _stale(target: str, deps) -> bool:
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(HERE, "..", "include", "stkde.h"))
+    inc = os.path.join(HERE, "..", "include")
+    headers += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

@@ -52,6 +52,7 @@ struct ProblemDev {
     uint32_t key_base;        // first bin key of the problem (its keys: key_base .. key_base + nkeys)
     int64_t ev_base;          // first event of the problem in the batch's event numbering
     int64_t item_base;        // first tile of the problem in the batch's tile numbering
+    int64_t fitem_base;       // the same in the fp32 tile kernel's numbering (64-voxel T blocks)
     const float4* ev;         // the batch's events sorted by key
     const uint32_t* start;    // the problem's bin boundaries start[0 .. nkeys]
     float* out;               // the problem's output grid, device memory
@@ -116,6 +117,12 @@ void launch_count_updates(const float4* ev, int n, const Plan& pl, double hsv, d
 
 // ------------------------------------------------------------ tile_fp32.cu
 void launch_tile_fp32(const Plan& pl, const Bins& b, float* out, int* err, cudaStream_t st);
+// Tiles of the fp32 tile kernel for one problem.
+int64_t tile_fp32_items(const Plan& pl);
+// The fp32 tile kernel over every problem of a batch in one launch: `table` in
+// device memory with fitem_base set to the running sum of tile_fp32_items;
+// problems with n = 0 get zeros.  Returns false for 2^31 tiles or more.
+bool launch_tile_fp32_batch(const ProblemDev* table, int nprob, int64_t total_items, cudaStream_t st);
 
 // -------------------------------------------------------------- scatter.cu
 void launch_scatter(const Plan& pl, const float4* ev, float* out, cudaStream_t st);
@@ -133,14 +140,27 @@ size_t tile_order_bytes_items(int64_t items);
 // tx0, ntxg: only the tiles of tile columns tx0 .. tx0 + ntxg - 1 (ntxg 0: all), so
 // that a grid can be computed in slabs of X whose copies overlap later slabs.
 // form: 0 bf16x3, 1 fp16x3, 2 tf32x3, 3 tf32x1 (the last two with fixed bandwidths only).
+// wait: the bound of the kernel's waits in ns (0: the default of 2 s) and, for
+// tests of the timeout path only, whether block 0 withholds the arrival of its
+// first staging page (no copy is issued into that page).
+struct TcWait {
+    uint64_t wait_ns = 0;
+    int withhold_page = 0;
+};
 bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* tile_ctr,
-                    uint32_t* order_ws, int form, cudaStream_t st, int tx0 = 0, int ntxg = 0);
+                    uint32_t* order_ws, int form, cudaStream_t st, int tx0 = 0, int ntxg = 0,
+                    TcWait wait = TcWait{});
 // The same over the tiles of all problems of a batch in one launch: `table` is
 // the batch's problem table in device memory (nprob entries, item_base set to
 // the running sum of tile_tc_items), total_items the sum; order_ws holds
 // tile_order_bytes_items(total_items).
 bool launch_tile_tc_batch(const ProblemDev* table, int nprob, int64_t total_items, int* err,
-                          int* tile_ctr, uint32_t* order_ws, int form, cudaStream_t st);
+                          int* tile_ctr, uint32_t* order_ws, int form, cudaStream_t st,
+                          TcWait wait = TcWait{});
+// Copies a host problem table into device memory through kernel parameters (up
+// to 64 entries per launch), so that the copy needs no host buffer that outlives
+// the call (and can be captured into a CUDA graph).  Returns the launches.
+int launch_table_upload(const ProblemDev* host, int count, ProblemDev* dev, cudaStream_t st);
 // K0 over all events of a batch: event i belongs to the problem whose ev_base
 // range holds it; keys are offset by the problem's key_base.
 void launch_recentre_batch(const ProblemDev* table, int nprob, int ntotal, float4* ev,

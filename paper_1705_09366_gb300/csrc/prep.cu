@@ -10,6 +10,8 @@
 // single contiguous run of events.
 #include "internal.cuh"
 
+#include <string.h>
+
 namespace stkde {
 
 // ------------------------------------------------------------------- K0 ---
@@ -114,6 +116,37 @@ void launch_recentre_batch(const ProblemDev* table, int nprob, int ntotal, float
                            uint32_t* keys, uint32_t* idx, int* err, cudaStream_t st) {
     if (ntotal <= 0 || nprob <= 0) return;
     k_recentre_batch<<<(ntotal + 255) / 256, 256, 0, st>>>(table, nprob, ntotal, ev, keys, idx, err);
+}
+
+// ------------------------------------------------------- table upload ---
+// The batch's problem table travels as kernel parameters: the launch copies the
+// argument values at enqueue time, so no host buffer has to outlive the call and
+// the copy can be captured into a graph (a captured cudaMemcpyAsync would read
+// its host source at every replay instead).
+constexpr int UPLOAD_CHUNK = 64;  // entries per launch (about 14 KB of parameters)
+
+struct TableChunk {
+    ProblemDev p[UPLOAD_CHUNK];
+};
+
+__global__ void k_table_upload(TableChunk chunk, int count, ProblemDev* __restrict__ dst) {
+    constexpr int WORDS = sizeof(ProblemDev) / sizeof(uint32_t);
+    static_assert(sizeof(ProblemDev) % sizeof(uint32_t) == 0, "table entries are whole words");
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(chunk.p);
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    for (int w = threadIdx.x; w < count * WORDS; w += blockDim.x) d[w] = src[w];
+}
+
+int launch_table_upload(const ProblemDev* host, int count, ProblemDev* dev, cudaStream_t st) {
+    int launches = 0;
+    for (int i = 0; i < count; i += UPLOAD_CHUNK) {
+        const int m = count - i < UPLOAD_CHUNK ? count - i : UPLOAD_CHUNK;
+        TableChunk c;
+        memcpy(c.p, host + i, sizeof(ProblemDev) * (size_t)m);
+        k_table_upload<<<1, 256, 0, st>>>(c, m, dev + i);
+        ++launches;
+    }
+    return launches;
 }
 
 // ---------------------------------------------------------- radix sort ---

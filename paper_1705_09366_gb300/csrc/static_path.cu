@@ -14,9 +14,11 @@
 // cudaMalloc, cudaFree or other allocating routine.
 //
 // The array's name is only a host-side stand-in for the device memory, so its
-// device address is looked up with cudaGetSymbolAddress, once per device, on the
-// first call made while that device is current; that first call should come
-// before any stream capture.  Every call on a device shares the one array and
+// device address is looked up with cudaGetSymbolAddress on every call made
+// outside stream capture (a context reset gives the array a new address); a
+// call made during a capture uses the address the last call on that device
+// found, so the first call on a device must come before any capture.  Every
+// call on a device shares the one array and
 // each call overwrites what the previous one left (the error word is cleared at
 // the start of every call): calls whose work overlaps on the GPU -- two streams,
 // two host threads -- race with each other and must be serialised by the caller.
@@ -60,11 +62,12 @@ constexpr int kMaxDevices = 64;
 unsigned char* g_dev_scratch[kMaxDevices] = {};
 std::mutex g_setup_mutex;
 
-// Device address of the scratch on the current device (looked up once per device).
-stkde_status scratch_for_device(int dev, unsigned char** out) {
+// Device address of the scratch on the current device: looked up again outside
+// stream capture, the last address found on the device during a capture.
+stkde_status scratch_for_device(int dev, bool capture, unsigned char** out) {
     if (dev < 0 || dev >= kMaxDevices) return STKDE_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_dev_scratch[dev]) {
+    if (!capture) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) {
@@ -72,9 +75,20 @@ stkde_status scratch_for_device(int dev, unsigned char** out) {
             return STKDE_ERR_CUDA;
         }
         g_dev_scratch[dev] = static_cast<unsigned char*>(p);
+    } else if (!g_dev_scratch[dev]) {
+        return STKDE_ERR_UNSUPPORTED;  // no call on this device preceded the capture
     }
     *out = g_dev_scratch[dev];
     return STKDE_OK;
+}
+
+bool stream_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
 }
 
 // The tensor tile kernel's form code of an API tensor form.
@@ -114,11 +128,13 @@ extern "C" stkde_status stkde_compute_static(const double* points, int64_t n,
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return STKDE_ERR_CUDA; }
     if (!is_device_pointer(out, dev)) return STKDE_ERR_INVALID_ARGUMENT;
     if (n > 0 && !is_device_pointer(points, dev)) return STKDE_ERR_INVALID_ARGUMENT;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool capture = stream_capturing(st);
+    if (capture && sync) return STKDE_ERR_UNSUPPORTED;  // a captured call cannot wait
     unsigned char* base = nullptr;
-    s = scratch_for_device(dev, &base);
+    s = scratch_for_device(dev, capture, &base);
     if (s != STKDE_OK) return s;
 
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     float4* ev = reinterpret_cast<float4*>(base + kOffEv);
     float4* ev_sorted = reinterpret_cast<float4*>(base + kOffEvSorted);
     uint32_t* keys = reinterpret_cast<uint32_t*>(base + kOffKeys);

@@ -9,6 +9,7 @@
 #include <new>
 
 #include "../../include/stkde.h"
+#include "../../include/stkde_testing.h"
 #include "internal.cuh"
 
 using namespace stkde;
@@ -50,6 +51,10 @@ struct stkde_ctx {
     cudaEvent_t copy_done = nullptr;
     bool slabs_ok = false;
     int launches = 0;          // kernels enqueued by the last compute call
+    // test hooks (stkde_inject_fault): the allocation that fails (countdown, 0 =
+    // none) and the next tensor tile launch's wait bound and withheld page
+    int fail_alloc = 0;
+    TcWait tc_wait{};
 };
 
 namespace {
@@ -164,16 +169,55 @@ stkde_status cuda_status(cudaError_t e) {
     return STKDE_ERR_CUDA;
 }
 
-stkde_status ensure_ws(stkde_ctx* c, size_t bytes) {
-    if (bytes <= c->ws_bytes) return STKDE_OK;
+// True while the context's stream is being captured into a CUDA graph: nothing
+// may then allocate, wait for the stream or copy from pageable host memory.
+bool capturing(const stkde_ctx* c) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Every device buffer a context grows is allocated here.  The test hook of
+// stkde_inject_fault makes the k-th allocation from now on fail as it would on
+// a device out of memory.
+cudaError_t ctx_malloc(stkde_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (c->fail_alloc > 0 && --c->fail_alloc == 0) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+    }
+    return e;
+}
+
+// Grows the context buffer *buf (of *have bytes) to hold `bytes`, allocating
+// `want` >= bytes.  The old buffer is freed first (after the stream drains), so
+// a failed growth leaves the buffer empty: nothing leaks and a later call
+// starts over.  Under stream capture a buffer cannot grow: UNSUPPORTED.
+stkde_status grow(stkde_ctx* c, void** buf, size_t* have, size_t bytes, size_t want) {
+    if (bytes <= *have) return STKDE_OK;
+    if (capturing(c)) return STKDE_ERR_UNSUPPORTED;
     cudaStreamSynchronize(c->stream);
-    if (c->ws) cudaFree(c->ws);
-    c->ws = nullptr; c->ws_bytes = 0;
-    const size_t want = align_up(bytes + bytes / 8, 1 << 20);
-    cudaError_t e = cudaMalloc(&c->ws, want);
-    if (e != cudaSuccess) { cudaGetLastError(); c->ws = nullptr; return STKDE_ERR_OOM; }
-    c->ws_bytes = want;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (ctx_malloc(c, buf, want) != cudaSuccess) return STKDE_ERR_OOM;
+    *have = want;
     return STKDE_OK;
+}
+
+stkde_status ensure_ws(stkde_ctx* c, size_t bytes) {
+    return grow(c, &c->ws, &c->ws_bytes, bytes, align_up(bytes + bytes / 8, 1 << 20));
+}
+
+// The context's device result buffer (host outputs, the pilot of
+// stkde_abramson_bandwidths).
+stkde_status ensure_out_tmp(stkde_ctx* c, size_t bytes) {
+    return grow(c, reinterpret_cast<void**>(&c->out_tmp), &c->out_tmp_bytes, bytes, bytes);
 }
 
 // Is p a pointer the device can use directly?  Host (pageable or pinned) memory
@@ -244,9 +288,11 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
             nslab = nslab < MAX_SLABS ? nslab : MAX_SLABS;
             nslab = nslab < pl.ntx ? nslab : pl.ntx;
         }
+        const TcWait tw = c->tc_wait;  // a test hook applies to one launch
+        c->tc_wait = TcWait{};
         if (nslab < 2) {
             // heaviest tiles first (two small launches), then the tile kernel
-            if (!launch_tile_tc(pl, b, out, c->d_err, c->d_ctr, w.order, tcf, st))
+            if (!launch_tile_tc(pl, b, out, c->d_err, c->d_ctr, w.order, tcf, st, 0, 0, tw))
                 return STKDE_ERR_UNSUPPORTED;
             c->launches += 2;
         } else {
@@ -256,7 +302,7 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
             for (int k = 0; k <= nslab; ++k) lo[k] = (int)((int64_t)pl.ntx * k / nslab);
             for (int k = 0; k < nslab; ++k) {
                 if (!launch_tile_tc(pl, b, out, c->d_err, c->d_ctr, w.order, tcf, st, lo[k],
-                                    lo[k + 1] - lo[k]))
+                                    lo[k + 1] - lo[k], k == 0 ? tw : TcWait{}))
                     return STKDE_ERR_UNSUPPORTED;
                 cudaEventRecord(c->slab_ev[k], st);
             }
@@ -289,16 +335,8 @@ stkde_status stage_bandwidths(stkde_ctx* c, int64_t n, const double*& hs, const 
     const size_t nn = (size_t)n;
     const size_t need = sizeof(double) * ((hkind == 0 ? nn : 0) + (tkind == 0 ? nn : 0));
     if (need == 0) return STKDE_OK;
-    if (need > c->bw_stage_bytes) {
-        cudaStreamSynchronize(c->stream);
-        if (c->bw_stage) cudaFree(c->bw_stage);
-        c->bw_stage = nullptr; c->bw_stage_bytes = 0;
-        if (cudaMalloc(&c->bw_stage, need) != cudaSuccess) {
-            cudaGetLastError();
-            return STKDE_ERR_OOM;
-        }
-        c->bw_stage_bytes = need;
-    }
+    const stkde_status s = grow(c, reinterpret_cast<void**>(&c->bw_stage), &c->bw_stage_bytes, need, need);
+    if (s != STKDE_OK) return s;
     double* dst = c->bw_stage;
     cudaError_t e = cudaSuccess;
     if (hkind == 0) {
@@ -448,6 +486,7 @@ void stkde_destroy(stkde_ctx* c) {
 stkde_status stkde_synchronize(stkde_ctx* c) {
     if (!c) return STKDE_ERR_INVALID_ARGUMENT;
     cudaSetDevice(c->device);
+    if (capturing(c)) return STKDE_ERR_UNSUPPORTED;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_status(e);
     int h = 0;
@@ -468,19 +507,14 @@ stkde_status stkde_compute(stkde_ctx* c, const double* points, int64_t n, const 
     if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
     const int okind = pointer_kind(out, c->device);
     if (okind < 0) return STKDE_ERR_INVALID_ARGUMENT;
+    const bool cap = capturing(c);
+    if (cap && (okind == 0 || (n > 0 && pointer_kind(points, c->device) == 0)))
+        return STKDE_ERR_UNSUPPORTED;  // host buffers cannot be part of a graph
     const size_t grid_bytes = sizeof(float) * (size_t)g->gx * (size_t)g->gy * (size_t)g->gt;
     float* dout = out;
     if (okind == 0) {  // host output: compute into the context's buffer, copy back
-        if (grid_bytes > c->out_tmp_bytes) {
-            cudaStreamSynchronize(c->stream);
-            if (c->out_tmp) cudaFree(c->out_tmp);
-            c->out_tmp = nullptr; c->out_tmp_bytes = 0;
-            if (cudaMalloc(&c->out_tmp, grid_bytes) != cudaSuccess) {
-                cudaGetLastError();
-                return STKDE_ERR_OOM;
-            }
-            c->out_tmp_bytes = grid_bytes;
-        }
+        const stkde_status so = ensure_out_tmp(c, grid_bytes);
+        if (so != STKDE_OK) return so;
         dout = c->out_tmp;
     }
     c->nphase = 0;
@@ -538,6 +572,7 @@ stkde_status stkde_compute_adaptive(stkde_ctx* c, const double* points, int64_t 
         return STKDE_ERR_UNSUPPORTED;
     if (n == 0) return stkde_compute(c, points, 0, g, g->sres, g->tres, out);
     if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
+    if (capturing(c)) return STKDE_ERR_UNSUPPORTED;  // waits for the stream
     const int okind = pointer_kind(out, c->device);
     const int pkind = pointer_kind(points, c->device);
     const int hkind = pointer_kind(hs, c->device), tkind = pointer_kind(ht, c->device);
@@ -560,16 +595,8 @@ stkde_status stkde_compute_adaptive(stkde_ctx* c, const double* points, int64_t 
     const size_t grid_bytes = sizeof(float) * (size_t)g->gx * (size_t)g->gy * (size_t)g->gt;
     float* dout = out;
     if (okind == 0) {
-        if (grid_bytes > c->out_tmp_bytes) {
-            cudaStreamSynchronize(c->stream);
-            if (c->out_tmp) cudaFree(c->out_tmp);
-            c->out_tmp = nullptr; c->out_tmp_bytes = 0;
-            if (cudaMalloc(&c->out_tmp, grid_bytes) != cudaSuccess) {
-                cudaGetLastError();
-                return STKDE_ERR_OOM;
-            }
-            c->out_tmp_bytes = grid_bytes;
-        }
+        const stkde_status so = ensure_out_tmp(c, grid_bytes);
+        if (so != STKDE_OK) return so;
         dout = c->out_tmp;
     }
     // Bandwidth classes for the tensor forms: halvings of the largest spatial
@@ -632,6 +659,7 @@ stkde_status stkde_abramson_bandwidths(stkde_ctx* c, const double* points, int64
         !(isfinite(lam_max) && lam_max >= 1.0))
         return STKDE_ERR_INVALID_ARGUMENT;
     if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
+    if (capturing(c)) return STKDE_ERR_UNSUPPORTED;
     if (pilot && pointer_kind(pilot, c->device) != 1) return STKDE_ERR_INVALID_ARGUMENT;
     if (n == 0) return pilot ? stkde_compute(c, points, 0, g, hs, ht, pilot) : STKDE_OK;
     if (!hs_out || !ht_out || pointer_kind(hs_out, c->device) != 1 ||
@@ -642,16 +670,8 @@ stkde_status stkde_abramson_bandwidths(stkde_ctx* c, const double* points, int64
     const size_t grid_bytes = sizeof(float) * (size_t)g->gx * (size_t)g->gy * (size_t)g->gt;
     float* dpil = pilot;
     if (!dpil) {  // the context's result buffer holds the pilot
-        if (grid_bytes > c->out_tmp_bytes) {
-            cudaStreamSynchronize(c->stream);
-            if (c->out_tmp) cudaFree(c->out_tmp);
-            c->out_tmp = nullptr; c->out_tmp_bytes = 0;
-            if (cudaMalloc(&c->out_tmp, grid_bytes) != cudaSuccess) {
-                cudaGetLastError();
-                return STKDE_ERR_OOM;
-            }
-            c->out_tmp_bytes = grid_bytes;
-        }
+        const stkde_status so = ensure_out_tmp(c, grid_bytes);
+        if (so != STKDE_OK) return so;
         dpil = c->out_tmp;
     }
     s = stkde_compute(c, points, n, g, hs, ht, dpil);
@@ -678,10 +698,13 @@ stkde_status stkde_abramson_bandwidths(stkde_ctx* c, const double* points, int64
 // Batched compute: one re-centre, one binning sort and one bounds + gather pass
 // over the concatenated events of all problems (keys offset per problem, so the
 // sort groups events by problem, then by bin), then one tile-kernel launch whose
-// heaviest-first queue holds the tiles of every problem (tensor forms), or one
-// fp32 tile launch per problem.  Each problem's result equals its own
-// stkde_compute with the same form: the same kernels see the same events in the
-// same order.
+// tile queue holds the tiles of every problem (heaviest first with the tensor
+// forms; the fp32 form's grid numbers the tiles problem after problem).  Each
+// problem's result equals its own stkde_compute with the same form: the same
+// kernels see the same events in the same order.  The problem table reaches the
+// device as kernel parameters, so with device events and a workspace that
+// already fits, the call allocates nothing, waits for nothing and can be
+// captured into a CUDA graph.
 stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int count) {
     if (!c || (count > 0 && !probs) || count < 0) return STKDE_ERR_INVALID_ARGUMENT;
     if (count == 0) return STKDE_OK;
@@ -689,6 +712,7 @@ stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int c
     if (form == STKDE_FORM_SCATTER) return STKDE_ERR_UNSUPPORTED;
     const bool tensor = tc_form(form) >= 0;
     if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
+    const bool cap = capturing(c);
 
     // validate everything and lay the batch out before any launch
     ProblemDev* tab = new (std::nothrow) ProblemDev[count];
@@ -702,7 +726,7 @@ stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int c
         ProblemDev* t; int* k;
         ~Guard() { delete[] t; delete[] k; }
     } guard{tab, pkinds};
-    int64_t ntot = 0, itot = 0, host_events = 0;
+    int64_t ntot = 0, itot = 0, ftot = 0, host_events = 0;
     uint64_t ktot = 0;
     for (int i = 0; i < count; ++i) {
         const stkde_problem& q = probs[i];
@@ -711,6 +735,7 @@ stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int c
         if (!q.out || pointer_kind(q.out, c->device) != 1) return STKDE_ERR_INVALID_ARGUMENT;
         pkinds[i] = q.n > 0 ? pointer_kind(q.points, c->device) : 1;
         if (pkinds[i] < 0) return STKDE_ERR_INVALID_ARGUMENT;
+        if (pkinds[i] == 0 && cap) return STKDE_ERR_UNSUPPORTED;  // host events in a graph
         ProblemDev& P = tab[i];
         P = ProblemDev{};
         P.pl = make_plan(c->opt.kernel_constants, q.n, &q.grid, q.hs, q.ht, c->opt.slab);
@@ -722,11 +747,14 @@ stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int c
         P.key_base = (uint32_t)ktot;
         P.ev_base = ntot;
         P.item_base = itot;
+        P.fitem_base = ftot;
         ktot += (uint64_t)P.pl.nkeys + 1;  // the problem's bins and its "reaches nothing" key
         ntot += q.n;
         if (pkinds[i] == 0) host_events += q.n;
         if (tensor) itot += tile_tc_items(P.pl);
-        if (ntot >= ((int64_t)1 << 31) || ktot >= ((uint64_t)1 << 32) || itot >= ((int64_t)1 << 31))
+        else ftot += tile_fp32_items(P.pl);
+        if (ntot >= ((int64_t)1 << 31) || ktot >= ((uint64_t)1 << 32) || itot >= ((int64_t)1 << 31) ||
+            ftot >= ((int64_t)1 << 31))
             return STKDE_ERR_UNSUPPORTED;
     }
 
@@ -780,10 +808,7 @@ stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int c
         P.start = start + P.key_base;
         P.out = probs[i].out;
     }
-    // the table is staged by the driver before cudaMemcpyAsync returns (pageable source)
-    cudaError_t e = cudaMemcpyAsync(dtab, tab, sizeof(ProblemDev) * (size_t)count,
-                                    cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_status(e);
+    c->launches += launch_table_upload(tab, count, dtab, st);
     int key_bits = 1;
     while (key_bits < 32 && ((uint64_t)1 << key_bits) <= ktot - 1) ++key_bits;
 
@@ -798,19 +823,14 @@ stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int c
     c->launches += ntot > 0 ? 2 : 1;
     mark(c);
     if (tensor) {
-        if (!launch_tile_tc_batch(dtab, count, itot, c->d_err, c->d_ctr, order, tc_form(form), st))
+        const TcWait tw = c->tc_wait;
+        c->tc_wait = TcWait{};
+        if (!launch_tile_tc_batch(dtab, count, itot, c->d_err, c->d_ctr, order, tc_form(form), st, tw))
             return STKDE_ERR_UNSUPPORTED;
         c->launches += itot > 0 ? 3 : 0;
     } else {
-        for (int i = 0; i < count; ++i) {
-            const Plan& pl = tab[i].pl;
-            if (probs[i].n == 0) {
-                cudaMemsetAsync(probs[i].out, 0, sizeof(float) * (size_t)pl.gx * pl.gy * pl.gt, st);
-                continue;
-            }
-            launch_tile_fp32(pl, Bins{ev_sorted, start + tab[i].key_base}, probs[i].out, c->d_err, st);
-            c->launches += 1;
-        }
+        if (!launch_tile_fp32_batch(dtab, count, ftot, st)) return STKDE_ERR_UNSUPPORTED;
+        c->launches += ftot > 0 ? 1 : 0;
     }
     mark(c);
     return cuda_status(cudaGetLastError());
@@ -821,6 +841,7 @@ stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int c
 static stkde_status count_updates(stkde_ctx* c, const double* points, int64_t n,
                                   const stkde_grid* g, double hs, double ht, const double* hs_i,
                                   const double* ht_i, int hkind, int tkind, uint64_t* count) {
+    if (capturing(c)) return STKDE_ERR_UNSUPPORTED;  // synchronous
     const int pkind = pointer_kind(points, c->device);
     if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
     const Plan pl = make_plan(c->opt.kernel_constants, n, g, hs, ht, c->opt.slab);
@@ -879,6 +900,7 @@ stkde_status stkde_count_updates_adaptive(stkde_ctx* c, const double* points, in
     *count = 0;
     if (n == 0) return STKDE_OK;
     if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
+    if (capturing(c)) return STKDE_ERR_UNSUPPORTED;  // synchronous
     const int hkind = pointer_kind(hs, c->device), tkind = pointer_kind(ht, c->device);
     if (hkind < 0 || tkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
     s = stage_bandwidths(c, n, hs, ht, hkind, tkind);
@@ -892,6 +914,33 @@ stkde_status stkde_count_updates_adaptive(stkde_ctx* c, const double* points, in
 }
 
 int stkde_last_launch_count(stkde_ctx* c) { return c ? c->launches : 0; }
+
+stkde_status stkde_reserve(stkde_ctx* c, size_t bytes) {
+    if (!c) return STKDE_ERR_INVALID_ARGUMENT;
+    if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
+    return ensure_ws(c, bytes);
+}
+
+stkde_status stkde_inject_fault(stkde_ctx* c, int fault, int64_t arg) {
+    if (!c) return STKDE_ERR_INVALID_ARGUMENT;
+    switch (fault) {
+        case STKDE_FAULT_NONE:
+            c->fail_alloc = 0;
+            c->tc_wait = TcWait{};
+            return STKDE_OK;
+        case STKDE_FAULT_ALLOC:
+            if (arg < 1 || arg > (1 << 30)) return STKDE_ERR_INVALID_ARGUMENT;
+            c->fail_alloc = (int)arg;
+            return STKDE_OK;
+        case STKDE_FAULT_WITHHOLD_PAGE:
+            if (arg < 1 || arg > 2000000) return STKDE_ERR_INVALID_ARGUMENT;
+            c->tc_wait.wait_ns = (uint64_t)arg * 1000u;
+            c->tc_wait.withhold_page = 1;
+            return STKDE_OK;
+        default:
+            return STKDE_ERR_INVALID_ARGUMENT;
+    }
+}
 
 int stkde_phase_times(stkde_ctx* c, float* ms, int cap) {
     if (!c || !c->opt.profile || !c->events_ok || c->nphase < 2) return 0;

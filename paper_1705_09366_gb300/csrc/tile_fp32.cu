@@ -30,10 +30,14 @@ constexpr int F_HALF = 32;       // T accumulators per thread
 constexpr int F_BATCH = 128;     // events per K_t table
 constexpr int F_BUF = F_BATCH + F_THREADS;
 
-template <bool ADAPT>
+// With BATCH, block b computes tile b of the batch's fp32 tile numbering: the
+// problem is the last table entry whose fitem_base is <= b, and its plan, bins
+// and output replace the arguments.
+template <bool ADAPT, bool BATCH>
 __global__ void __launch_bounds__(F_THREADS, 2)
 k_tile_fp32(Plan pl, const float4* __restrict__ ev, const float4* __restrict__ evp,
-            const uint32_t* __restrict__ start, float* __restrict__ out) {
+            const uint32_t* __restrict__ start, float* __restrict__ out,
+            const ProblemDev* __restrict__ table, int nprob) {
     __shared__ float4 buf[F_BUF];
     __shared__ float4 bufp[ADAPT ? F_BUF : 1];  // per-event bandwidths of buf
     __shared__ __align__(16) float ktab[F_BATCH][F_TB];
@@ -42,7 +46,22 @@ k_tile_fp32(Plan pl, const float4* __restrict__ ev, const float4* __restrict__ e
     __shared__ int s_count;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t item = blockIdx.x;
+    int64_t item = blockIdx.x;
+    if constexpr (BATCH) {
+        int lo = 0, hi = nprob - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (table[mid].fitem_base <= item) lo = mid; else hi = mid - 1;
+        }
+        const ProblemDev& P = table[lo];
+        pl = P.pl;
+        pl.tblock = F_TB;
+        pl.ntb = (pl.gt + F_TB - 1) / F_TB;
+        ev = P.ev;
+        start = P.start;
+        out = P.out;
+        item -= P.fitem_base;
+    }
     const int ty = (int)(item % pl.nty);
     const int tx = (int)((item / pl.nty) % pl.ntx);
     const int tb = (int)(item / ((int64_t)pl.nty * pl.ntx));
@@ -195,9 +214,23 @@ void launch_tile_fp32(const Plan& pl, const Bins& b, float* out, int* err, cudaS
     const int64_t items = (int64_t)p.ntx * p.nty * p.ntb;
     if (items <= 0) return;
     if (b.evp)
-        k_tile_fp32<true><<<(unsigned)items, F_THREADS, 0, st>>>(p, b.ev, b.evp, b.start, out);
+        k_tile_fp32<true, false><<<(unsigned)items, F_THREADS, 0, st>>>(p, b.ev, b.evp, b.start, out,
+                                                                        nullptr, 0);
     else
-        k_tile_fp32<false><<<(unsigned)items, F_THREADS, 0, st>>>(p, b.ev, nullptr, b.start, out);
+        k_tile_fp32<false, false><<<(unsigned)items, F_THREADS, 0, st>>>(p, b.ev, nullptr, b.start, out,
+                                                                         nullptr, 0);
+}
+
+int64_t tile_fp32_items(const Plan& pl) {
+    return (int64_t)pl.ntx * pl.nty * ((pl.gt + F_TB - 1) / F_TB);
+}
+
+bool launch_tile_fp32_batch(const ProblemDev* table, int nprob, int64_t total_items, cudaStream_t st) {
+    if (nprob <= 0 || total_items <= 0) return true;
+    if (total_items >= ((int64_t)1 << 31)) return false;
+    k_tile_fp32<false, true><<<(unsigned)total_items, F_THREADS, 0, st>>>(Plan{}, nullptr, nullptr, nullptr,
+                                                                          nullptr, table, nprob);
+    return true;
 }
 
 }  // namespace stkde

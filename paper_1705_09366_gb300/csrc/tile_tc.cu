@@ -67,10 +67,12 @@
 // normalisation 1/(n hs_max^2 ht_max)).  The weight scales both the product and
 // the disk-test difference of A, so the mask is unchanged.
 //
-// Every wait on an mbarrier is bounded (2 s of %globaltimer); on expiry the
-// kernel sets the timeout bit of the error word, every role leaves its loop,
-// outstanding copies and MMAs are drained with a second bounded wait, and the
-// tensor memory is freed before the CTA exits.
+// Every wait on an mbarrier is bounded (2 s of %globaltimer, or the launch's
+// own bound); on expiry the kernel sets the timeout bit of the error word, every
+// role leaves its loop, outstanding copies and MMAs are drained with a second
+// bounded wait, and the tensor memory is freed before the CTA exits.  A test
+// hook makes block 0 withhold the arrival of its first staging page (issuing no
+// copy into it), so that this path can be exercised without a fault.
 #include "internal.cuh"
 #include "ptx.cuh"
 #include "tile_common.cuh"
@@ -159,7 +161,7 @@ struct L {
     static constexpr uint32_t OFF_BAR = OFF_DESC + NSTREAM * 16;
     static constexpr int BARS_PER_STREAM = 3 * NPAGES + 2 * NSTAGE + 4;
     static constexpr int NBARS = NSTREAM * BARS_PER_STREAM;
-    static constexpr uint32_t OFF_MISC = OFF_BAR + NBARS * 8;  // tmem base, abort flag
+    static constexpr uint32_t OFF_MISC = OFF_BAR + NBARS * 8;  // tmem base, abort flag, wait bound
     static constexpr uint32_t TOTAL = OFF_MISC + 16;
     // barrier indices of stream p
     __host__ __device__ static constexpr int pfull(int p, int q) { return p * BARS_PER_STREAM + q; }
@@ -278,12 +280,17 @@ __device__ __forceinline__ void commit_elect(uint32_t bar) {
 }
 
 struct Ctl {
-    volatile int* abort;
+    volatile int* abort;  // shared memory: the abort flag, then the wait bound (ns)
     int* err;
 };
 
+// The launch's bound on every wait, read only once a wait has spun a while.
+__device__ __forceinline__ uint64_t wait_limit(const Ctl& c) {
+    return *reinterpret_cast<const volatile uint64_t*>(c.abort + 1);
+}
+
 __device__ __forceinline__ bool timed_out(const Ctl& c, uint64_t t0) {
-    if (ptx::globaltimer() - t0 > WAIT_NS) {
+    if (ptx::globaltimer() - t0 > wait_limit(c)) {
         *c.abort = 1;
         atomicOr(c.err, ERRBIT_TIMEOUT);
         return true;
@@ -292,7 +299,7 @@ __device__ __forceinline__ bool timed_out(const Ctl& c, uint64_t t0) {
 }
 
 // Bounded wait for the phase of parity `parity` of barrier `bar`.  Returns
-// false (and raises the abort flag) after WAIT_NS, or as soon as another role
+// false (and raises the abort flag) after the wait bound, or as soon as another role
 // has aborted.
 __device__ __forceinline__ bool wait_bar(const Ctl& c, uint32_t bar, uint32_t parity) {
     if (ptx::mbar_try_wait(bar, parity)) return true;
@@ -351,7 +358,7 @@ template <int FORM, bool ADAPT>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
           int* __restrict__ err, int* __restrict__ tile_ctr, const uint32_t* __restrict__ order,
-          int64_t nitems, int flush_chunks) {
+          int64_t nitems, int flush_chunks, TcWait wc) {
     using C = Cfg<FORM>;
     constexpr int CHUNK = C::CHUNK;
     constexpr bool FP16 = C::FP16;
@@ -382,6 +389,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             ptx::mbar_init(bar(L::drain(p)), 1);
         }
         *c.abort = 0;
+        *reinterpret_cast<volatile uint64_t*>(smem + L::OFF_MISC + 8) = wc.wait_ns ? wc.wait_ns : WAIT_NS;
         ptx::fence_mbar_init();
     }
     if (warp == 0) {
@@ -398,6 +406,8 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
     if (load_stream(warp) >= 0) {
         // ------------------------------------------------------------ loader
         const int p = load_stream(warp);
+        // test hook: block 0's first page of stream 0 never arrives
+        const bool withhold = wc.withhold_page && blockIdx.x == 0 && p == 0;
         uint32_t pg = 0, fill = 0;
         bool open = false, ok = true;
         auto open_page = [&]() -> bool {
@@ -520,7 +530,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 pmeta[3 * q + 2] = ppl ? make_int4(__float_as_int(ppl->inv_hs), __float_as_int(ppl->inv_ht),
                                                    __float_as_int(ppl->hsv), __float_as_int(ppl->htv))
                                        : make_int4(0, 0, 0, 0);
-                ptx::mbar_arrive(bar(L::pfull(p, pg % NPAGES)));
+                if (!(withhold && pg == 0)) ptx::mbar_arrive(bar(L::pfull(p, pg % NPAGES)));
             }
             __syncwarp();
             ++pg;
@@ -577,7 +587,7 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                     // this page takes pass positions [done, done + take); each lane copies
                     // the part of its own run that falls there
                     const uint32_t lo = max(off, done), hi = min(off + len, done + take);
-                    if (hi > lo) {
+                    if (hi > lo && !(withhold && pg == 0)) {
                         const uint32_t fb = bar(L::pfull(p, pg % NPAGES));
                         const uint32_t dst = sb + L::OFF_PAGES + q * PAGE_BYTES + (fill + (lo - done)) * 16u;
                         ptx::mbar_expect_tx(fb, (hi - lo) * (ADAPT ? 32u : 16u));
@@ -587,7 +597,10 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                     }
                     fill += take;
                     done += take;
-                    if (fill == (uint32_t)PEV) close_page(0, item, tx, ty, tb, pi, &pl);
+                    if (fill == (uint32_t)PEV) {
+                        close_page(0, item, tx, ty, tb, pi, &pl);
+                        if (!ok) break;  // a wait gave up: stage nothing more
+                    }
                 }
             }
             }
@@ -1085,7 +1098,7 @@ __global__ void k_tile_order(int nitems, const uint32_t* __restrict__ cost,
 
 template <int FORM, bool ADAPT>
 bool launch_cfg(const ProblemDev& single, const ProblemDev* table, int nprob, int64_t items,
-                int* err, int* tile_ctr, uint32_t* order_ws, cudaStream_t st) {
+                int* err, int* tile_ctr, uint32_t* order_ws, cudaStream_t st, TcWait wc) {
     auto kern = k_tile_tc<FORM, ADAPT>;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -1125,7 +1138,7 @@ bool launch_cfg(const ProblemDev& single, const ProblemDev* table, int nprob, in
     // per step.
     const int flush_chunks = FORM == FORM_FP16X3 ? 64 : FORM == FORM_TF32X3 ? 32 : 128;
     kern<<<grid, NTHREADS, L::TOTAL, st>>>(single, table, nprob, err, tile_ctr, order, items,
-                                           flush_chunks);
+                                           flush_chunks, wc);
     return true;
 }
 
@@ -1145,26 +1158,26 @@ size_t tile_order_bytes(const Plan& pl) { return tile_order_bytes_items(tile_tc_
 // bandwidths with the 16-bit forms only).
 template <bool ADAPT>
 bool launch_form(int form, const ProblemDev& single, const ProblemDev* table, int nprob, int64_t items,
-                 int* err, int* tile_ctr, uint32_t* order_ws, cudaStream_t st) {
+                 int* err, int* tile_ctr, uint32_t* order_ws, cudaStream_t st, TcWait wc) {
     switch (form) {
         case FORM_BF16X3:
-            return launch_cfg<FORM_BF16X3, ADAPT>(single, table, nprob, items, err, tile_ctr, order_ws, st);
+            return launch_cfg<FORM_BF16X3, ADAPT>(single, table, nprob, items, err, tile_ctr, order_ws, st, wc);
         case FORM_FP16X3:
-            return launch_cfg<FORM_FP16X3, ADAPT>(single, table, nprob, items, err, tile_ctr, order_ws, st);
+            return launch_cfg<FORM_FP16X3, ADAPT>(single, table, nprob, items, err, tile_ctr, order_ws, st, wc);
         default:
             break;
     }
     if constexpr (!ADAPT) {
         if (form == FORM_TF32X3)
-            return launch_cfg<FORM_TF32X3, false>(single, table, nprob, items, err, tile_ctr, order_ws, st);
+            return launch_cfg<FORM_TF32X3, false>(single, table, nprob, items, err, tile_ctr, order_ws, st, wc);
         if (form == FORM_TF32X1)
-            return launch_cfg<FORM_TF32X1, false>(single, table, nprob, items, err, tile_ctr, order_ws, st);
+            return launch_cfg<FORM_TF32X1, false>(single, table, nprob, items, err, tile_ctr, order_ws, st, wc);
     }
     return false;
 }
 
 bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* tile_ctr,
-                    uint32_t* order_ws, int form, cudaStream_t st, int tx0, int ntxg) {
+                    uint32_t* order_ws, int form, cudaStream_t st, int tx0, int ntxg, TcWait wc) {
     ProblemDev single{};
     single.pl = pl;
     single.ev = b.ev;
@@ -1175,15 +1188,15 @@ bool launch_tile_tc(const Plan& pl, const Bins& b, float* out, int* err, int* ti
     single.tx0 = tx0;
     single.ntxg = ntxg;
     const int64_t items = ntxg > 0 ? tile_tc_items(pl) / pl.ntx * ntxg : tile_tc_items(pl);
-    if (b.evp) return launch_form<true>(form, single, nullptr, 1, items, err, tile_ctr, order_ws, st);
-    return launch_form<false>(form, single, nullptr, 1, items, err, tile_ctr, order_ws, st);
+    if (b.evp) return launch_form<true>(form, single, nullptr, 1, items, err, tile_ctr, order_ws, st, wc);
+    return launch_form<false>(form, single, nullptr, 1, items, err, tile_ctr, order_ws, st, wc);
 }
 
 bool launch_tile_tc_batch(const ProblemDev* table, int nprob, int64_t total_items, int* err,
-                          int* tile_ctr, uint32_t* order_ws, int form, cudaStream_t st) {
+                          int* tile_ctr, uint32_t* order_ws, int form, cudaStream_t st, TcWait wc) {
     if (nprob <= 0) return true;
     const ProblemDev none{};
-    return launch_form<false>(form, none, table, nprob, total_items, err, tile_ctr, order_ws, st);
+    return launch_form<false>(form, none, table, nprob, total_items, err, tile_ctr, order_ws, st, wc);
 }
 
 }  // namespace stkde

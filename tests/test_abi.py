@@ -1,4 +1,4 @@
-"""The C ABI library builds, loads and exports what include/stkde.h declares.
+"""The C ABI library builds, loads and exports what include/*.h declare.
 
 These tests run without a GPU: they launch no compute.  Calls that need a
 device must fail cleanly with a status code.
@@ -22,8 +22,12 @@ def libstkde():
 
 
 def declared_symbols():
-    with open(os.path.join(ROOT, "include", "stkde.h")) as f:
-        text = f.read()
+    inc = os.path.join(ROOT, "include")
+    text = ""
+    for name in sorted(os.listdir(inc)):
+        if name.endswith(".h"):
+            with open(os.path.join(inc, name)) as f:
+                text += f.read()
     return sorted(set(re.findall(r"STKDE_API\s+[\w\s\*]*?\b(stkde_\w+)\s*\(", text)))
 
 
@@ -67,6 +71,8 @@ def test_null_arguments_are_rejected_without_a_device(libstkde):
     assert libstkde.stkde_create(None, None) == pkg.ERR_INVALID_ARGUMENT
     assert libstkde.stkde_synchronize(None) == pkg.ERR_INVALID_ARGUMENT
     assert libstkde.stkde_phase_times(None, None, 0) == 0
+    assert libstkde.stkde_reserve(None, 1 << 20) == pkg.ERR_INVALID_ARGUMENT
+    assert libstkde.stkde_inject_fault(None, pkg.FAULT_ALLOC, 1) == pkg.ERR_INVALID_ARGUMENT
     libstkde.stkde_destroy(None)
 
 

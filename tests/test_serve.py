@@ -49,3 +49,31 @@ def test_form_batch_admits_in_order_within_budget():
 def test_percentiles():
     p = serve.percentiles([0.001 * k for k in range(1, 101)])
     assert abs(p["p50_ms"] - 50.5) < 1e-9 and abs(p["p99_ms"] - 99.01) < 1e-9 and p["max_ms"] == 100.0
+
+
+def test_form_batch_without_force_waits_for_room():
+    # with batches already running, an oversized first request waits
+    big = [_req(0, 512), _req(1, 64)]
+    assert serve.form_batch(big, budget_bytes=1 << 20, set_bytes=lambda s: 0, force_first=False) == []
+    assert [r.rid for r in serve.form_batch(big, budget_bytes=1 << 30, set_bytes=lambda s: 0,
+                                            force_first=False)] == [0, 1]
+
+
+def test_expire_drops_cancelled_and_late_requests_in_place():
+    q = [serve.Request(0, 0, 8, 8, 8, 1.0, 1.0, 5.0, 4.0, 0.0, deadline=0.5),
+         serve.Request(1, 0, 8, 8, 8, 1.0, 1.0, 5.0, 4.0, 0.2),
+         serve.Request(2, 0, 8, 8, 8, 1.0, 1.0, 5.0, 4.0, 0.3, deadline=0.5),
+         serve.Request(3, 0, 8, 8, 8, 1.0, 1.0, 5.0, 4.0, 0.4)]
+    gone = serve.expire(q, now=0.6, cancelled={3})
+    assert [r.rid for r in gone] == [0, 3]          # 0 is late (0.6 > 0.0 + 0.5); 3 cancelled
+    assert [r.rid for r in q] == [1, 2]             # 2 is not late yet (0.6 <= 0.8), order kept
+    assert serve.expire(q, now=0.81, cancelled=set())[0].rid == 2 and [r.rid for r in q] == [1]
+
+
+def test_overlap_of_intervals():
+    assert serve.overlap([]) == {"max_concurrent": 0, "overlap_time": 0.0}
+    assert serve.overlap([(0.0, 1.0), (2.0, 3.0)]) == {"max_concurrent": 1, "overlap_time": 0.0}
+    o = serve.overlap([(0.0, 2.0), (1.0, 3.0), (1.5, 1.75)])
+    assert o["max_concurrent"] == 3 and abs(o["overlap_time"] - 1.0) < 1e-12
+    # touching intervals do not overlap
+    assert serve.overlap([(0.0, 1.0), (1.0, 2.0)])["max_concurrent"] == 1

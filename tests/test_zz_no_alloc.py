@@ -4,7 +4,11 @@ It serves callers that cannot call cudaMalloc (another component owns every
 device allocation, or their loop must not take cudaMalloc's device-wide
 synchronisation).  Checked here through the C ABI: two calls in a row, each
 compared with the allocating stkde_compute on the same inputs within the
-tolerances of the parity tests, and the size limits refused before any launch.
+tolerances of the parity tests; the device's free memory is the same before and
+after a call; a call captured into a CUDA graph in global capture mode (where a
+cudaMalloc would invalidate the capture) replays to the same bits; a call with
+sync = 0 on a side stream completes with that stream; and the size limits are
+refused before any launch.
 This file is collected last, so a run that stops at the first failure has run
 every other test first; it also passes on its own in a fresh process.
 """
@@ -37,7 +41,8 @@ def _allocating(form, w, pts):
 
 
 @pytest.mark.parametrize("wname,form", [("small", "bf16x3"), ("small", "fp32"),
-                                        ("small", "fp16x3"), ("medium", "bf16x3")])
+                                        ("small", "fp16x3"), ("small", "scatter"),
+                                        ("medium", "bf16x3")])
 def test_static_entry_matches_allocating_entry_twice(wname, form):
     w = synth.WORKLOADS[wname]()
     pts = torch.from_numpy(w.points).cuda()
@@ -50,6 +55,46 @@ def test_static_entry_matches_allocating_entry_twice(wname, form):
         assert not torch.isnan(out).any().item()
         err = float((out.double() - ref).abs().max()) / scale
         assert err <= pu.TOL[form], err
+
+
+def test_static_entry_allocates_nothing():
+    w = synth.small()
+    pts = torch.from_numpy(w.points).cuda()
+    grid = pkg.make_grid(w.gx, w.gy, w.gt)
+    out = torch.empty((w.gx, w.gy, w.gt), dtype=torch.float32, device="cuda")
+    pkg.stkde_compute_static(pts, w.n, grid, w.hs, w.ht, out, sync=True)  # modules loaded
+    ref = out.clone()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    pkg.stkde_compute_static(pts, w.n, grid, w.hs, w.ht, out, sync=True)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.equal(out, ref)
+
+    # captured in global mode (any cudaMalloc in the call would invalidate the capture)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="global"):
+        pkg.stkde_compute_static(pts, w.n, grid, w.hs, w.ht, out, stream=s, sync=False)
+    out.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    # a captured call cannot wait for its stream
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=s, capture_error_mode="global"):
+        out.zero_()
+        with pytest.raises(pkg.StkdeError) as e:
+            pkg.stkde_compute_static(pts, w.n, grid, w.hs, w.ht, out, stream=s, sync=True)
+        assert e.value.status == pkg.ERR_UNSUPPORTED
+
+    # sync = 0 on a side stream: the result is there once that stream is done
+    side = torch.cuda.Stream()
+    out.fill_(float("nan"))
+    torch.cuda.synchronize()
+    pkg.stkde_compute_static(pts, w.n, grid, w.hs, w.ht, out, stream=side, sync=False)
+    side.synchronize()
+    assert torch.equal(out, ref)
 
 
 def test_static_entry_refuses_sizes_beyond_its_scratch():
