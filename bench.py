@@ -42,8 +42,16 @@ METRIC = "STKDE voxel-updates/s & ms/grid vs plain GPU at stated err; serve p50/
 UNIT = "voxel-point updates/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                   "sm_max_mhz": 2070.0}
-ERR_GATE = {"bf16x3": 2e-5, "fp16x3": 1e-5, "fp32": 1e-5, "scatter": 1e-5}
-PRODUCTS = {"bf16x3": 3, "fp16x3": 3, "fp32": 1, "scatter": 1}
+# error gates (max |gpu - oracle| / grid max after the tie slack); the one-product
+# tf32 form is reported without a gate
+ERR_GATE = {"bf16x3": 2e-5, "fp16x3": 1e-5, "tf32x3": 1e-5, "tf32x1": None, "fp32": 1e-5,
+            "scatter": 1e-5}
+PRODUCTS = {"bf16x3": 3, "fp16x3": 3, "tf32x3": 3, "tf32x1": 1, "fp32": 1, "scatter": 1}
+DTYPE = {"bf16x3": "bf16", "fp16x3": "f16", "tf32x3": "tf32", "tf32x1": "tf32", "fp32": "f32",
+         "scatter": "f32"}
+TENSOR_FORMS = ("bf16x3", "fp16x3", "tf32x3", "tf32x1")
+# nominal dense tensor rates relative to bf16 (2.25 PFLOP/s): tf32 1.1 PFLOP/s
+NOMINAL_RATIO = {"bf16x3": 1.0, "fp16x3": 1.0, "tf32x3": 1.1 / 2.25, "tf32x1": 1.1 / 2.25}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -54,12 +62,12 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(synth.WORKLOADS), default="large")
-    ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "fp16x3", "fp32", "scatter"])
-    ap.add_argument("--compare", default="fp16x3,fp32,scatter",
+    ap.add_argument("--form", default="bf16x3", choices=list(ERR_GATE))
+    ap.add_argument("--compare", default="fp16x3,tf32x3,tf32x1,fp32,scatter",
                     help="other forms timed beside the main one ('' for none)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--bandwidth", choices=["fixed", "adaptive", "abramson"], default="fixed",
                     help="adaptive: per-event bandwidths log-uniform in [h/spread, h*spread]; "
                          "abramson: from a pilot density by Abramson's law, factors clamped "
@@ -67,9 +75,14 @@ def parse_args():
     ap.add_argument("--spread", type=float, default=2.0)
     ap.add_argument("--batch-count", type=int, default=64,
                     help="instances of the batched workload timed beside the main line (0: skip)")
-    ap.add_argument("--serve-requests", type=int, default=600,
+    ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests of the serving run reported beside the main line (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-load-requests", type=int, default=4000,
+                    help="requests of a second serving run at --serve-load-rate (0: skip)")
+    ap.add_argument("--serve-load-rate", type=float, default=800.0)
+    ap.add_argument("--medium", type=int, default=1,
+                    help="also time the medium workload in the main form (0: skip)")
     return ap.parse_args()
 
 
@@ -387,13 +400,15 @@ def run_ours(args):
     grid_bytes = 4 * w.gx * w.gy * w.gt
     prods = PRODUCTS[args.form]
     flops = 2.0 * prods * updates
-    if args.form in ("bf16x3", "fp16x3"):
-        peak = peaks["bf16_tflops"]
+    if args.form in TENSOR_FORMS:
+        peak = peaks["bf16_tflops"] * NOMINAL_RATIO[args.form]
         roof = {"bound": "tensor", "unit": "TFLOP/s",
                 "achieved": flops / (tile_ms * 1e-3) / 1e12, "peak": peak}
         roof["frac"] = roof["achieved"] / peak
+        own = "bf16" if NOMINAL_RATIO[args.form] == 1.0 else \
+            f"tf32 (= bf16 x {NOMINAL_RATIO[args.form]:.3f}, the nominal dense-rate ratio)"
         roof["note"] = (f"algorithmic FLOPs = 2 x {prods} products x {updates} voxel-point "
-                        f"updates; peak = {peaks_src} dense bf16 (burst)")
+                        f"updates; peak = {peaks_src} dense {own} (burst)")
         # the same kernel against the FP32 CUDA-core roofline (one FMA per update)
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         fp32_fma = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
@@ -437,11 +452,19 @@ def run_ours(args):
         del hout, hpts
 
     # ---- other forms on the same input (rank 0, N = 1)
-    forms = {args.form: {"ms_per_grid": ms_per_step, "updates_per_s": value / max(world, 1),
-                         "tile_kernel_ms": tile_ms}}
+    def form_entry(f, ms, tms):
+        e = {"ms_per_grid": ms, "updates_per_s": updates / (ms * 1e-3), "tile_kernel_ms": tms}
+        if f in TENSOR_FORMS and tms == tms:
+            fpk = peaks["bf16_tflops"] * NOMINAL_RATIO[f]
+            e["tensor_tflops"] = 2.0 * PRODUCTS[f] * updates / (tms * 1e-3) / 1e12
+            e["frac_of_own_peak"] = e["tensor_tflops"] / fpk
+        return e
+
+    forms = {args.form: form_entry(args.form, ms_per_step, tile_ms)}
+    forms[args.form]["updates_per_s"] = value / max(world, 1)
     if rank == 0 and world == 1 and args.compare:
         for f in [x for x in args.compare.split(",")
-                  if x and x != args.form and not (adaptive and x == "scatter")]:
+                  if x and x != args.form and not (adaptive and x in ("scatter", "tf32x3", "tf32x1"))]:
             fo = torch.empty(dims, dtype=torch.float32, device=dev)
             with pkg.Context(device=local, stream=stream, form=f) as fc:
                 reps = 1 if f == "scatter" else 3
@@ -456,13 +479,25 @@ def run_ours(args):
                     s1.record(stream)
                     fc.synchronize()
                     tot += s0.elapsed_time(s1)
-                forms[f] = {"ms_per_grid": tot / reps, "updates_per_s": updates / (tot / reps * 1e-3)}
+            with pkg.Context(device=local, stream=stream, form=f, profile=True) as pc:
+                flush.fill_(0.5)
+                compute(pc, pts, fo)
+                pt = pc.phase_times()
+                pc.synchronize()
+            forms[f] = form_entry(f, tot / reps, pt[3] if len(pt) > 3 else float("nan"))
             forms[f]["_out"] = fo
+
+    # ---- the medium workload in the main form (rank 0, N = 1)
+    medium = None
+    if rank == 0 and world == 1 and args.medium and not adaptive:
+        medium = run_medium(pkg, torch, dev, stream, args.form, peaks, peaks_src, flush)
 
     # ---- CPU oracle baseline + error against it on the sampled tiles (rank 0, N = 1)
     cpu = None
     errs = {}
     if rank == 0 and world == 1 and not args.no_cpu:
+        if medium is not None:
+            medium_error(medium)
         import oracle
         pairs, dt, boxes, res, _ = oracle_sample(w, args.cpu_seconds, seed=rank,
                                                  bw=(hs_h, ht_h) if adaptive else None)
@@ -484,23 +519,27 @@ def run_ours(args):
                 worst = max(worst, float(ex / scale))
             errs[f] = worst
             forms[f]["max_rel_err"] = worst
-            forms[f]["err_gate"] = ERR_GATE[f]
+            forms[f]["err_gate"] = ERR_GATE[f] if ERR_GATE[f] is not None else "report only"
     for v in forms.values():
         v.pop("_out", None)
+    if medium is not None:
+        medium.pop("_out", None)
 
     # ---- batched workload and serving loop (rank 0, N = 1)
-    batch = serve = None
+    batch = serve = serve_load = None
     if rank == 0 and world == 1 and args.batch_count > 0:
-        batch = run_batch(pkg, torch, stream, args.form, args.batch_count)
+        batch = run_batch(pkg, torch, args.form, args.batch_count)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         serve = run_serve(args.form, args.serve_requests, args.serve_rate)
+    if rank == 0 and world == 1 and args.serve_load_requests > 0:
+        serve_load = run_serve(args.form, args.serve_load_requests, args.serve_load_rate)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"bf16x3": "bf16", "fp16x3": "f16", "fp32": "f32", "scatter": "f32"}[args.form],
+            "dtype": DTYPE[args.form],
             "data": "synthetic",
             "config": {"workload": wname, "n": w.n, "grid": [w.gx, w.gy, w.gt], "hs": w.hs,
                        "ht": w.ht, "bandwidth": bandwidth_label(args),
@@ -514,8 +553,10 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "forms": forms,
+            "medium": medium,
             "batch": batch,
             "serve": serve,
+            "serve_load": serve_load,
             "max_rel_err": errs.get(args.form),
             "peaks": peaks_src,
         }
@@ -526,14 +567,97 @@ def run_ours(args):
     return 0
 
 
-def run_batch(pkg, torch, stream, form, count):
+def densest_tiles(w, k):
+    """The k 16 x 8 x gt tile boxes holding the most events (input statistics)."""
+    cx = np.floor((w.points[:, 0] - w.x0) / w.sres / 16).astype(np.int64)
+    cy = np.floor((w.points[:, 1] - w.y0) / w.sres / 8).astype(np.int64)
+    nx, ny = (w.gx + 15) // 16, (w.gy + 7) // 8
+    ok = (cx >= 0) & (cx < nx) & (cy >= 0) & (cy < ny)
+    h = np.bincount(cx[ok] * ny + cy[ok], minlength=nx * ny)
+    return [(int(c // ny) * 16, min(w.gx, int(c // ny) * 16 + 16), int(c % ny) * 8,
+             min(w.gy, int(c % ny) * 8 + 8), 0, w.gt) for c in np.argsort(h)[::-1][:k]]
+
+
+def run_medium(pkg, torch, dev, stream, form, peaks, peaks_src, flush, steps=10):
+    """The medium workload (n = 200,000, 512 x 512 x 256, hs 10, ht 8) in the main
+    form: ms per grid with the L2 flushed before each step (CUDA events), the
+    tile kernel's time from the library's phase events, its output write rate
+    and the fraction of the HBM floor (the 268 MB grid written once at the
+    measured copy bandwidth).  The grid is kept (key "_out") for medium_error."""
+    w = synth.medium()
+    dims = (w.gx, w.gy, w.gt)
+    pts = torch.from_numpy(w.points).to(dev)
+    out = torch.empty(dims, dtype=torch.float32, device=dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    with pkg.Context(device=dev.index, stream=stream, form=form) as c:
+        updates = c.count_updates(pts, dims, w.hs, w.ht)
+        for _ in range(3):
+            c.compute(pts, dims, w.hs, w.ht, out=out)
+        c.synchronize()
+        for i in range(steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            c.compute(pts, dims, w.hs, w.ht, out=out)
+            ends[i].record(stream)
+        c.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in zip(starts, ends))
+    tiles = []
+    with pkg.Context(device=dev.index, stream=stream, form=form, profile=True) as c:
+        for i in range(steps):
+            flush.fill_(float(i))
+            c.compute(pts, dims, w.hs, w.ht, out=out)
+            tiles.append(c.phase_times()[3])
+        c.synchronize()
+    tile_ms = statistics.mean(tiles)
+    grid_bytes = 4 * w.gx * w.gy * w.gt
+    floor_ms = 1e3 * grid_bytes / (peaks["hbm_gbs"] * 1e9)
+    res = {"workload": w.name, "form": form, "updates_per_grid": int(updates), "ms_per_grid": ms,
+           "updates_per_s": updates / (ms * 1e-3), "tile_kernel_ms": tile_ms,
+           "hbm_write_gbs": grid_bytes / (tile_ms * 1e-3) / 1e9,
+           "hbm_floor_ms": floor_ms, "frac_of_hbm_floor": floor_ms / tile_ms,
+           "peak_source": peaks_src, "l2": "flushed before each step (256 MiB write)"}
+    if form in TENSOR_FORMS:
+        res["tensor_tflops"] = 2.0 * PRODUCTS[form] * updates / (tile_ms * 1e-3) / 1e12
+    res["_out"] = out
+    return res
+
+
+def medium_error(medium):
+    """Max error of the medium grid against the FP64 oracle on 24 sampled tiles
+    (the 8 densest, 16 random), part of the CPU-oracle leg."""
+    import oracle
+    w = synth.medium()
+    out = medium["_out"]
+    rng = np.random.default_rng(7)
+    boxes = densest_tiles(w, 8)
+    allb = tile_boxes(w, seed=7)
+    for k in rng.permutation(len(allb))[:16]:
+        if allb[k] not in boxes:
+            boxes.append(allb[k])
+    p = oracle.params(w.gx, w.gy, w.gt, w.hs, w.ht)
+    refs = oracle.pb_boxes(w.points, p, boxes, with_slack=True)
+    scale = max(r.max() for r, _ in refs)
+    worst = 0.0
+    for (x0, x1, y0, y1, t0, t1), (ref, slack) in zip(boxes, refs):
+        got = out[x0:x1, y0:y1, t0:t1].double().cpu().numpy()
+        worst = max(worst, float(np.maximum(np.abs(got - ref) - slack, 0.0).max() / scale))
+    f = medium["form"]
+    medium["max_rel_err"] = worst
+    medium["err_gate"] = ERR_GATE[f] if ERR_GATE[f] is not None else "report only"
+    medium["err_sample"] = f"{len(boxes)} tiles of 16x8x{w.gt}"
+
+
+def run_batch(pkg, torch, form, count):
     """The batched workload: `count` uneven instances in one stkde_compute_batch
-    call against the same problems in one stkde_compute call each (CUDA events,
-    3 repetitions after 2 warm-up batches, no L2 flush: the instances are small)."""
+    call against the same problems in one stkde_compute call each, and the batch
+    captured once into a CUDA graph and replayed (CUDA events, 3 repetitions after
+    2 warm-up batches, no L2 flush: the instances are small)."""
     ws = synth.batched(count=count)
     pts = [torch.from_numpy(w.points).cuda() for w in ws]
     outs = [torch.empty((w.gx, w.gy, w.gt), dtype=torch.float32, device="cuda") for w in ws]
     probs = [(p, (w.gx, w.gy, w.gt), w.hs, w.ht, o) for p, w, o in zip(pts, ws, outs)]
+    stream = torch.cuda.Stream()  # capture needs a stream other than the legacy one
     with pkg.Context(stream=stream, form=form) as c:
         for _ in range(2):
             c.compute_batch(probs)
@@ -553,10 +677,38 @@ def run_batch(pkg, torch, stream, form, count):
         s1.record(stream)
         c.synchronize()
         t_single = s0.elapsed_time(s1) / 3
+        # the batch as a CUDA graph: captured once, replayed
+        c.compute_batch(probs)
+        c.synchronize()
+        direct = [o.clone() for o in outs]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            c.compute_batch(probs)
+        with torch.cuda.stream(stream):  # replays run on torch's current stream
+            for o in outs:
+                o.fill_(float("nan"))
+            g.replay()
+            stream.synchronize()
+            identical = all(torch.equal(o, d) for o, d in zip(outs, direct))
+            s0.record(stream)
+            for _ in range(3):
+                g.replay()
+            s1.record(stream)
+            stream.synchronize()
+        t_graph = s0.elapsed_time(s1) / 3
+        # host time to enqueue one batch (what the graph removes)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        c.compute_batch(probs)
+        t_enqueue = 1e3 * (time.perf_counter() - t)
+        c.synchronize()
         updates = sum(c.count_updates(p, (w.gx, w.gy, w.gt), w.hs, w.ht) for p, w in zip(pts, ws))
     return {"workload": f"{count} uneven instances (n log-uniform 1e3..5e5, grids 64^3..512x512x128)",
+            "form": form,
             "events": int(sum(w.n for w in ws)), "voxels": int(sum(w.gx * w.gy * w.gt for w in ws)),
             "updates": int(updates), "ms_per_batch": t_batch, "ms_single_calls": t_single,
+            "ms_per_batch_graph_replay": t_graph, "graph_replay_bit_identical": identical,
+            "host_enqueue_ms": t_enqueue,
             "updates_per_s": updates / (t_batch * 1e-3), "launches_per_batch": launches}
 
 
@@ -570,7 +722,8 @@ def run_serve(form, n_requests, rate):
     srv.run(srvmod.request_stream(8, 1000.0, len(sets), seed=99))
     stats, _, _, _ = srv.run(srvmod.request_stream(n_requests, rate, len(sets), seed=0))
     srv.close()
-    stats.update({"rate_hz": rate, "sets": [int(s.shape[0]) for s in sets]})
+    stats.update({"rate_hz": rate, "offered": n_requests, "sets": [int(s.shape[0]) for s in sets]})
+    stats["dropped"] = len(stats["dropped"])
     return stats
 
 

@@ -1,0 +1,159 @@
+"""Per-problem launch configuration chosen from measured timings.
+
+The library exposes two choices that change speed but not the definition of
+the density: the tensor form (each within its own accuracy gate) and the T
+extent of an event bin (``slab``: how many voxels of T one bin spans; fewer,
+longer bins mean fewer bin runs per tile but more events that the tile filter
+rejects).  Which is fastest depends on the problem's shape -- events, grid and
+bandwidths in voxels -- so the tuner times the candidates on the caller's own
+problem the first time it meets a shape and caches the winner in a JSON table
+keyed by the shape (and the device name).  Later calls of the same shape use the
+cached configuration without timing.
+
+Not tuned, and why:
+- the drift-flush count of the tensor forms: a larger count is faster but
+  lets the round-toward-zero drift of the tensor-core accumulation grow; each
+  form's count is the largest that keeps it within its accuracy gate, so any
+  faster choice would break the gate;
+- the tile shape and column-window width: compile-time constants of the tile
+  kernels (they size shared and tensor memory).
+
+All timing runs through the library's own kernels (CUDA events on the
+context's stream); the tuner holds no arithmetic of the density.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from typing import Callable, Optional
+
+# forms and the accuracy gate each one meets (max error / grid max)
+FORM_GATES = {"bf16x3": 2e-5, "fp16x3": 1e-5, "tf32x3": 1e-5, "fp32": 1e-5}
+SLABS = (0, 2, 8, 16)  # 0: the library's automatic choice (4 voxels of T, grown for huge grids)
+
+
+def shape_key(device_name: str, n: int, dims, hs_vox: float, ht_vox: float) -> str:
+    """Cache key: device, events rounded to a power of two, grid, bandwidths in
+    voxels rounded to two significant digits."""
+    nb = 0 if n <= 0 else int(round(math.log2(n)))
+
+    def r2(v):
+        return float(f"{v:.2g}")
+
+    gx, gy, gt = (int(d) for d in dims)
+    return f"{device_name}|n2^{nb}|{gx}x{gy}x{gt}|hs{r2(hs_vox)}|ht{r2(ht_vox)}"
+
+
+def candidates(max_err: float, forms=None):
+    """(form, slab) pairs whose form meets the accuracy target."""
+    fs = [f for f, g in FORM_GATES.items() if g <= max_err and (forms is None or f in forms)]
+    return [(f, s) for f in fs for s in SLABS]
+
+
+def pick(timings: dict) -> tuple:
+    """The fastest configuration; ties go to the first listed."""
+    best, best_ms = None, math.inf
+    for cfg, ms in timings.items():
+        if ms < best_ms:
+            best, best_ms = cfg, ms
+    return best
+
+
+class Table:
+    """The JSON cache: shape key -> {"form", "slab", "ms", "timings"}."""
+
+    def __init__(self, path: Optional[str]):
+        self.path = path
+        self.entries = {}
+        if path and os.path.exists(path):
+            with open(path) as f:
+                self.entries = json.load(f)
+
+    def get(self, key):
+        e = self.entries.get(key)
+        return (e["form"], int(e["slab"])) if e else None
+
+    def put(self, key, cfg, timings):
+        self.entries[key] = {"form": cfg[0], "slab": cfg[1], "ms": timings[cfg],
+                             "timings": {f"{f}/{s}": ms for (f, s), ms in timings.items()}}
+        if self.path:
+            tmp = self.path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(self.entries, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
+
+
+class Tuner:
+    """Computes densities with the fastest measured configuration for each
+    problem shape.  ``max_err`` selects the forms allowed (default 2e-5: all
+    tensor forms with three products, and fp32); ``cache`` is the JSON file of
+    the table (None: in memory only)."""
+
+    def __init__(self, device: int = 0, stream=None, max_err: float = 2e-5,
+                 cache: Optional[str] = None, reps: int = 3, forms=None):
+        import torch
+        import paper_1705_09366_gb300 as pkg
+
+        self.torch, self.pkg = torch, pkg
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.cands = candidates(max_err, forms)
+        if not self.cands:
+            raise ValueError(f"no form meets max_err={max_err}")
+        self.table = Table(cache)
+        self.reps = int(reps)
+        self.ctxs = {}
+        self.name = torch.cuda.get_device_name(device)
+
+    def _ctx(self, cfg):
+        if cfg not in self.ctxs:
+            self.ctxs[cfg] = self.pkg.Context(device=self.device, stream=self.stream, form=cfg[0],
+                                              slab=cfg[1])
+        return self.ctxs[cfg]
+
+    def _time(self, cfg, run: Callable):
+        torch = self.torch
+        c = self._ctx(cfg)
+        run(c)  # warm-up (sizes the workspace)
+        c.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(self.stream)
+        for _ in range(self.reps):
+            run(c)
+        s1.record(self.stream)
+        c.synchronize()
+        return s0.elapsed_time(s1) / self.reps
+
+    def config(self, points, dims, hs, ht, sres=1.0, tres=1.0, out=None):
+        """The configuration for this problem's shape: cached, or measured now
+        (each candidate computes the caller's problem into ``out``)."""
+        key = shape_key(self.name, int(points.shape[0]), dims, hs / sres, ht / tres)
+        cfg = self.table.get(key)
+        if cfg is not None and cfg in self.cands:
+            return cfg, key
+        if out is None:
+            out = self.torch.empty(tuple(int(d) for d in dims), dtype=self.torch.float32,
+                                   device=f"cuda:{self.device}")
+        timings = {}
+        for cand in self.cands:
+            timings[cand] = self._time(cand, lambda c: c.compute(points, dims, hs, ht, out=out,
+                                                                 sres=sres, tres=tres))
+        cfg = pick(timings)
+        self.table.put(key, cfg, timings)
+        return cfg, key
+
+    def compute(self, points, dims, hs, ht, out=None, origin=(0.0, 0.0, 0.0), sres=1.0, tres=1.0):
+        """Density of ``points`` with the tuned configuration (see Context.compute)."""
+        cfg, _ = self.config(points, dims, hs, ht, sres=sres, tres=tres, out=out)
+        return self._ctx(cfg).compute(points, dims, hs, ht, out=out, origin=origin, sres=sres,
+                                      tres=tres)
+
+    def synchronize(self):
+        for c in self.ctxs.values():
+            c.synchronize()
+
+    def close(self):
+        for c in self.ctxs.values():
+            c.close()
+        self.ctxs = {}

@@ -116,7 +116,8 @@ void launch_count_updates(const float4* ev, int n, const Plan& pl, double hsv, d
                           unsigned long long* count, cudaStream_t st);
 
 // ------------------------------------------------------------ tile_fp32.cu
-void launch_tile_fp32(const Plan& pl, const Bins& b, float* out, int* err, cudaStream_t st);
+// Returns false if the grid has 2^31 tiles or more or the kernel cannot be set up.
+bool launch_tile_fp32(const Plan& pl, const Bins& b, float* out, int* err, cudaStream_t st);
 // Tiles of the fp32 tile kernel for one problem.
 int64_t tile_fp32_items(const Plan& pl);
 // The fp32 tile kernel over every problem of a batch in one launch: `table` in

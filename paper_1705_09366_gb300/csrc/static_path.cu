@@ -161,7 +161,7 @@ extern "C" stkde_status stkde_compute_static(const double* points, int64_t n,
             launch_bounds_gather(keys, idx, ev, (int)n, pl.nkeys, start, ev_sorted, st);
             Bins b{ev_sorted, start};
             if (form == STKDE_FORM_FP32) {
-                launch_tile_fp32(pl, b, out, err, st);
+                if (!launch_tile_fp32(pl, b, out, err, st)) return STKDE_ERR_UNSUPPORTED;
             } else if (!launch_tile_tc(pl, b, out, err, tile_ctr, nullptr, static_tc_form(form), st)) {
                 return STKDE_ERR_UNSUPPORTED;
             }

@@ -277,7 +277,7 @@ stkde_status enqueue(stkde_ctx* c, const double* dpts, const Plan& pl, const stk
     mark(c);
     Bins b{w.ev_sorted, w.start, evp ? evp_sorted : nullptr};
     if (form == STKDE_FORM_FP32) {
-        launch_tile_fp32(pl, b, out, c->d_err, st);
+        if (!launch_tile_fp32(pl, b, out, c->d_err, st)) return STKDE_ERR_UNSUPPORTED;
     } else {
         const int tcf = tc_form(form);
         const size_t row_bytes = sizeof(float) * (size_t)pl.gy * (size_t)pl.gt;  // one X row

@@ -799,7 +799,9 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 // B = K_t without c_t: (1 - w^2)_+ for the window's columns
                 {
                     constexpr int EH = CHUNK / 2;   // events of one core-matrix row (16 bytes)
-                    const int hh = lane & 1;        // events EH hh .. EH hh + EH - 1
+                    // lanes 8h .. 8h + 7 of each 16 write events EH hh .. EH hh + EH - 1 of 8
+                    // consecutive columns: 128 contiguous bytes per 8 lanes, no bank conflict
+                    const int hh = (lane >> 3) & 1;
                     float2 tq[EH / 2], iq[EH / 2];
 #pragma unroll
                     for (int i = 0; i < EH / 4; ++i) {
@@ -815,8 +817,8 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                     const float2 ih2 = make_float2(inv_ht, inv_ht), one2 = make_float2(1.0f, 1.0f);
                     uint8_t* bh = st + 2 * A_BYTES;
                     uint8_t* bl = bh + B_BYTES;
-                    for (int it = lane; it < 2 * ncols; it += 32) {
-                        const int n = it >> 1;
+                    // columns n0, n0 + 16, ... (ncols is a multiple of 16)
+                    for (int n = ((lane >> 4) << 3) | (lane & 7); n < ncols; n += 16) {
                         const float2 n2 = make_float2((float)n, (float)n);
                         uint32_t h[4], l[4];
 #pragma unroll
