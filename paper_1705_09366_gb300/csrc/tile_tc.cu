@@ -985,7 +985,8 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
             const ProblemDev P = fetch_problem(single, table, dsc.y);
             const Plan& pl = P.pl;
             float* __restrict__ out = P.out;
-            const bool vec = (pl.gt & 3) == 0;
+            // float4 loads and stores need every voxel column 16-byte aligned
+            const bool vec = (pl.gt & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
             // A and B carry neither c_s nor c_t: both join the normalisation here
             const float scale = pl.norm * (pl.cs * pl.ct);
             const bool last = (dsc.z & D_LAST) != 0;
