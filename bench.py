@@ -526,7 +526,9 @@ def run_ours(args):
         medium.pop("_out", None)
 
     # ---- batched workload and serving loop (rank 0, N = 1)
-    batch = serve = serve_load = None
+    batch = serve = serve_load = tune = None
+    if rank == 0 and world == 1 and args.medium and not adaptive:
+        tune = run_tune(pkg, torch, dev)
     if rank == 0 and world == 1 and args.batch_count > 0:
         batch = run_batch(pkg, torch, args.form, args.batch_count)
     if rank == 0 and world == 1 and args.serve_requests > 0:
@@ -555,6 +557,7 @@ def run_ours(args):
             "forms": forms,
             "medium": medium,
             "batch": batch,
+            "tune": tune,
             "serve": serve,
             "serve_load": serve_load,
             "max_rel_err": errs.get(args.form),
@@ -703,13 +706,44 @@ def run_batch(pkg, torch, form, count):
         t_enqueue = 1e3 * (time.perf_counter() - t)
         c.synchronize()
         updates = sum(c.count_updates(p, (w.gx, w.gy, w.gt), w.hs, w.ht) for p, w in zip(pts, ws))
+    # the fp32 form's batch (one tile launch over all problems), one warm-up, two timed
+    fp32_ms = None
+    if form != "fp32":
+        with pkg.Context(stream=stream, form="fp32") as c:
+            c.compute_batch(probs)
+            c.synchronize()
+            s0.record(stream)
+            for _ in range(2):
+                c.compute_batch(probs)
+            s1.record(stream)
+            c.synchronize()
+            fp32_ms = s0.elapsed_time(s1) / 2
     return {"workload": f"{count} uneven instances (n log-uniform 1e3..5e5, grids 64^3..512x512x128)",
             "form": form,
             "events": int(sum(w.n for w in ws)), "voxels": int(sum(w.gx * w.gy * w.gt for w in ws)),
             "updates": int(updates), "ms_per_batch": t_batch, "ms_single_calls": t_single,
             "ms_per_batch_graph_replay": t_graph, "graph_replay_bit_identical": identical,
-            "host_enqueue_ms": t_enqueue,
+            "host_enqueue_ms": t_enqueue, "fp32_ms_per_batch": fp32_ms,
             "updates_per_s": updates / (t_batch * 1e-3), "launches_per_batch": launches}
+
+
+def run_tune(pkg, torch, dev):
+    """The autotuner on the medium workload (accuracy target 2e-5): every candidate
+    (form x bin slab) timed on the problem, the winner, and the default
+    configuration's time from the same table (no L2 flush between repetitions)."""
+    from paper_1705_09366_gb300 import autotune
+
+    w = synth.medium()
+    pts = torch.from_numpy(w.points).to(dev)
+    dims = (w.gx, w.gy, w.gt)
+    t = autotune.Tuner(device=dev.index or 0, reps=3)
+    try:
+        cfg, key = t.config(pts, dims, w.hs, w.ht)
+        e = t.table.entries[key]
+    finally:
+        t.close()
+    return {"workload": w.name, "candidates": len(e["timings"]), "chosen": {"form": cfg[0], "slab": cfg[1]},
+            "chosen_ms": e["ms"], "default_ms": e["timings"].get("bf16x3/0"), "timings_ms": e["timings"]}
 
 
 def run_serve(form, n_requests, rate):

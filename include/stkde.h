@@ -107,7 +107,9 @@ typedef struct {
     int kernel_constants;  /* stkde_kernel_constants */
     int t_block;           /* reserved, must be 0 (tiles span 256 voxels of T in the tensor
                               forms and 64 in the fp32 form) */
-    int slab;              /* T extent of an event bin: 0 = automatic, else >= 1 */
+    int slab;              /* T extent of an event bin: 0 = automatic (tensor forms: the
+                              smallest power of two from 4 to 16 giving at least 3.5
+                              events per bin on average; fp32 form: 64), else >= 1 */
     int profile;           /* 1: time each phase with CUDA events (see stkde_phase_times) */
 } stkde_options;
 
@@ -232,7 +234,7 @@ STKDE_API int stkde_last_launch_count(stkde_ctx* ctx);
 
 /* Largest problem stkde_compute_static accepts: events, and bin boundaries
  * (number of event bins + 1; a bin is 16 x 8 voxels in the plane by a slab of
- * 4 voxels of T, so roughly gx*gy*gt/512 bins). */
+ * at least 4 voxels of T, so at most about gx*gy*gt/512 bins). */
 #define STKDE_STATIC_MAX_EVENTS 262144
 #define STKDE_STATIC_MAX_BINS 1048576
 

@@ -30,7 +30,7 @@ from typing import Callable, Optional
 
 # forms and the accuracy gate each one meets (max error / grid max)
 FORM_GATES = {"bf16x3": 2e-5, "fp16x3": 1e-5, "tf32x3": 1e-5, "fp32": 1e-5}
-SLABS = (0, 2, 8, 16)  # 0: the library's automatic choice (4 voxels of T, grown for huge grids)
+SLABS = (0, 4, 8, 16, 32)  # 0: the library's automatic choice
 
 
 def shape_key(device_name: str, n: int, dims, hs_vox: float, ht_vox: float) -> str:

@@ -30,7 +30,7 @@
 namespace stkde {
 stkde_status check_problem_args(const double* points, int64_t n, const stkde_grid* g, double hs,
                                 double ht);
-Plan plan_problem(int kernel_constants, int64_t n, const stkde_grid* g, double hs, double ht);
+Plan plan_problem(int kernel_constants, int64_t n, const stkde_grid* g, double hs, double ht, int form);
 }  // namespace stkde
 
 using namespace stkde;
@@ -120,7 +120,7 @@ extern "C" stkde_status stkde_compute_static(const double* points, int64_t n,
     if (s != STKDE_OK) return s;
     if ((size_t)n > kMaxEvents || radix_sort_temp_bytes((int)n) > kHistBytes)
         return STKDE_ERR_UNSUPPORTED;  // beyond the fixed scratch
-    const Plan pl = plan_problem(kernel_constants, n, grid, hs, ht);
+    const Plan pl = plan_problem(kernel_constants, n, grid, hs, ht, form);
     if ((size_t)pl.nkeys + 1 > kMaxBins) return STKDE_ERR_UNSUPPORTED;  // too many bins
     if (form == STKDE_FORM_SCATTER && 2.0 * ceil(ht / grid->tres) + 1.0 > 12000.0)
         return STKDE_ERR_UNSUPPORTED;
