@@ -230,3 +230,19 @@ def test_output_only_4_byte_aligned(form):
     else:
         assert torch.equal(shifted, ref)
     assert torch.isnan(raw[0]).item() and torch.isnan(raw[1 + n:]).all().item()
+
+
+@pytest.mark.parametrize("form", ["bf16x3", "tf32x3", "fp32"])
+@pytest.mark.parametrize("slab", [1, 2, 8, 32, 64, 1000])
+def test_explicit_slabs(form, slab):
+    """Every bin slab (the T extent of an event bin, including one longer than the
+    grid's T extent) gives the density within the gate: the slab changes the
+    binning and the summation order, never the set of events a voxel sums."""
+    for name in ("ragged", "wide_t", "origin_res"):
+        case = next(e for e in EDGE if e[0] == name)
+        _, n, dims, hs, ht, origin, sres, tres = case
+        w = _case(name, np.random.default_rng(zlib.crc32(name.encode())), n, dims, hs * sres,
+                  ht * tres, origin, sres, tres)
+        ref, slack = oracle_full(w)
+        got = run(form, w, slab=slab).cpu().numpy()
+        assert pu.excess_error(got, ref, slack) <= pu.TOL[form], (name, slab)
