@@ -8,6 +8,8 @@
 
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/stkde.h"
 #include "../../include/stkde_testing.h"
 #include "internal.cuh"
@@ -25,6 +27,17 @@ constexpr int MAX_SLABS = 16;
 constexpr size_t SLAB_MIN_BYTES = (size_t)64 << 20;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Each entry point's host-side work (checks, planning, enqueueing) is an NVTX range
+// named after it, so profilers (Nsight Systems, Nsight Compute's --nvtx filters)
+// can attribute launches to calls; without an attached tool a range costs a
+// function-pointer check.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace
 
@@ -502,6 +515,7 @@ void stkde_destroy(stkde_ctx* c) {
 }
 
 stkde_status stkde_synchronize(stkde_ctx* c) {
+    const NvtxRange nvtx_range("stkde_synchronize");
     if (!c) return STKDE_ERR_INVALID_ARGUMENT;
     cudaSetDevice(c->device);
     if (capturing(c)) return STKDE_ERR_UNSUPPORTED;
@@ -519,6 +533,7 @@ stkde_status stkde_synchronize(stkde_ctx* c) {
 
 stkde_status stkde_compute(stkde_ctx* c, const double* points, int64_t n, const stkde_grid* g,
                            double hs, double ht, float* out) {
+    const NvtxRange nvtx_range("stkde_compute");
     if (!c || !out) return STKDE_ERR_INVALID_ARGUMENT;
     stkde_status s = check_problem(points, n, g, hs, ht);
     if (s != STKDE_OK) return s;
@@ -581,6 +596,7 @@ stkde_status stkde_compute(stkde_ctx* c, const double* points, int64_t n, const 
 stkde_status stkde_compute_adaptive(stkde_ctx* c, const double* points, int64_t n,
                                     const stkde_grid* g, const double* hs, const double* ht,
                                     float* out) {
+    const NvtxRange nvtx_range("stkde_compute_adaptive");
     if (!c || !out || !g) return STKDE_ERR_INVALID_ARGUMENT;
     if (n > 0 && (!hs || !ht)) return STKDE_ERR_INVALID_ARGUMENT;
     // grid and event checks (the bandwidths are checked below)
@@ -671,6 +687,7 @@ stkde_status stkde_abramson_bandwidths(stkde_ctx* c, const double* points, int64
                                        const stkde_grid* g, double hs, double ht, double alpha,
                                        double lam_min, double lam_max, float* pilot,
                                        double* hs_out, double* ht_out) {
+    const NvtxRange nvtx_range("stkde_abramson_bandwidths");
     if (!c || !g) return STKDE_ERR_INVALID_ARGUMENT;
     stkde_status s = check_problem(points, n, g, hs, ht);
     if (s != STKDE_OK) return s;
@@ -725,6 +742,7 @@ stkde_status stkde_abramson_bandwidths(stkde_ctx* c, const double* points, int64
 // already fits, the call allocates nothing, waits for nothing and can be
 // captured into a CUDA graph.
 stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int count) {
+    const NvtxRange nvtx_range("stkde_compute_batch");
     if (!c || (count > 0 && !probs) || count < 0) return STKDE_ERR_INVALID_ARGUMENT;
     if (count == 0) return STKDE_OK;
     const int form = c->opt.form;
@@ -902,6 +920,7 @@ static stkde_status count_updates(stkde_ctx* c, const double* points, int64_t n,
 
 stkde_status stkde_count_updates(stkde_ctx* c, const double* points, int64_t n,
                                  const stkde_grid* g, double hs, double ht, uint64_t* count) {
+    const NvtxRange nvtx_range("stkde_count_updates");
     if (!c || !count) return STKDE_ERR_INVALID_ARGUMENT;
     stkde_status s = check_problem(points, n, g, hs, ht);
     if (s != STKDE_OK) return s;
@@ -914,6 +933,7 @@ stkde_status stkde_count_updates(stkde_ctx* c, const double* points, int64_t n,
 stkde_status stkde_count_updates_adaptive(stkde_ctx* c, const double* points, int64_t n,
                                           const stkde_grid* g, const double* hs, const double* ht,
                                           uint64_t* count) {
+    const NvtxRange nvtx_range("stkde_count_updates_adaptive");
     if (!c || !count || !g) return STKDE_ERR_INVALID_ARGUMENT;
     if (n > 0 && (!hs || !ht)) return STKDE_ERR_INVALID_ARGUMENT;
     stkde_status s = check_problem(points, n, g, g->sres, g->tres);
@@ -937,6 +957,7 @@ stkde_status stkde_count_updates_adaptive(stkde_ctx* c, const double* points, in
 int stkde_last_launch_count(stkde_ctx* c) { return c ? c->launches : 0; }
 
 stkde_status stkde_reserve(stkde_ctx* c, size_t bytes) {
+    const NvtxRange nvtx_range("stkde_reserve");
     if (!c) return STKDE_ERR_INVALID_ARGUMENT;
     if (cudaSetDevice(c->device) != cudaSuccess) return STKDE_ERR_CUDA;
     return ensure_ws(c, bytes);
