@@ -109,7 +109,8 @@ typedef struct {
                               forms and 64 in the fp32 form) */
     int slab;              /* T extent of an event bin: 0 = automatic (tensor forms: the
                               smallest power of two from 4 to 16 giving at least 3.5
-                              events per bin on average; fp32 form: 64), else >= 1 */
+                              events per bin on average, 1.8 for the tf32 forms; fp32
+                              form: 64), else >= 1 */
     int profile;           /* 1: time each phase with CUDA events (see stkde_phase_times) */
 } stkde_options;
 

@@ -141,24 +141,28 @@ stkde_status check_problem(const double* points, int64_t n, const stkde_grid* g,
 // The T extent of an event bin when the caller leaves it to the library. Shorter
 // slabs mean more bin runs per tile for the loader to walk, longer ones more staged
 // events that the tile filter rejects; measured on GB300 (small, medium and large
-// workloads, slabs 2 to 64), the tensor forms do best with the smallest power of two
-// from 4 to 16 that puts at least 3.5 events in an average bin, and the fp32 form,
-// whose block-synchronous bin walk pays more per run, with 64.
-int default_slab(int64_t n, int ntx, int nty, int gt, bool fp32) {
-    if (fp32) return 64;
+// workloads, slabs 2 to 64), the kind::f16 forms do best with the smallest power of
+// two from 4 to 16 that puts at least 3.5 events in an average bin, the kind::tf32
+// forms (twice the MMA entries per event, so staged events that the filter rejects
+// cost them more) with at least 1.8, and the fp32 form, whose block-synchronous bin
+// walk pays more per run, with 64.
+int default_slab(int64_t n, int ntx, int nty, int gt, int form) {
+    if (form == STKDE_FORM_FP32) return 64;
+    const double per_bin =
+        (form == STKDE_FORM_TENSOR_TF32X3 || form == STKDE_FORM_TENSOR_TF32X1) ? 1.8 : 3.5;
     int slab = 4;
     while (slab < 16) {
         const double bins = (double)ntx * (double)nty * (double)((gt + slab - 1) / slab);
-        if ((double)n >= 3.5 * bins) break;
+        if ((double)n >= per_bin * bins) break;
         slab *= 2;
     }
     return slab;
 }
 
 // ncls_s x ncls_t bandwidth classes (per-event bandwidths; 1 x 1 otherwise).
-// fp32: the plan is for the fp32 tile kernel (only the default slab depends on it).
+// form: the stkde_form the plan is for (only the default slab depends on it).
 Plan make_plan(int kernel_constants, int64_t n, const stkde_grid* g, double hs, double ht,
-               int slab_opt, bool fp32, int ncls_s = 1, int ncls_t = 1) {
+               int slab_opt, int form, int ncls_s = 1, int ncls_t = 1) {
     Plan p{};
     p.gx = (int)g->gx; p.gy = (int)g->gy; p.gt = (int)g->gt;
     const double hsv = hs / g->sres, htv = ht / g->tres;
@@ -174,7 +178,7 @@ Plan make_plan(int kernel_constants, int64_t n, const stkde_grid* g, double hs, 
     p.ncls_s = ncls_s;
     p.ncls_t = ncls_t;
     const uint64_t ncls = (uint64_t)ncls_s * (uint64_t)ncls_t;
-    int slab = slab_opt > 0 ? slab_opt : default_slab(n, p.ntx, p.nty, p.gt, fp32);
+    int slab = slab_opt > 0 ? slab_opt : default_slab(n, p.ntx, p.nty, p.gt, form);
     slab = slab < p.gt ? slab : p.gt;
     while (true) {
         const uint64_t ns = (uint64_t)((p.gt + slab - 1) / slab);
@@ -413,7 +417,7 @@ stkde_status check_problem_args(const double* points, int64_t n, const stkde_gri
     return check_problem(points, n, g, hs, ht);
 }
 Plan plan_problem(int kernel_constants, int64_t n, const stkde_grid* g, double hs, double ht, int form) {
-    return make_plan(kernel_constants, n, g, hs, ht, 0, form == STKDE_FORM_FP32);
+    return make_plan(kernel_constants, n, g, hs, ht, 0, form);
 }
 }  // namespace stkde
 
@@ -562,8 +566,7 @@ stkde_status stkde_compute(stkde_ctx* c, const double* points, int64_t n, const 
         }
         const int pkind = pointer_kind(points, c->device);
         if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
-        const Plan pl = make_plan(c->opt.kernel_constants, n, g, hs, ht, c->opt.slab,
-                                  c->opt.form == STKDE_FORM_FP32);
+        const Plan pl = make_plan(c->opt.kernel_constants, n, g, hs, ht, c->opt.slab, c->opt.form);
         Workspace w;
         const bool tensor = tc_form(c->opt.form) >= 0;
         const size_t order_bytes = tensor ? tile_order_bytes(pl) : 0;
@@ -645,7 +648,7 @@ stkde_status stkde_compute_adaptive(stkde_ctx* c, const double* points, int64_t 
     if (tensor)
         while (ncls_s < 3 && hi[0] / lo[0] > (double)(1 << ncls_s)) ++ncls_s;
     const Plan pl = make_plan(c->opt.kernel_constants, n, g, hi[0], hi[1],
-                              c->opt.slab > 0 ? c->opt.slab : (ncls_s > 1 ? 8 : 0), !tensor, ncls_s, 1);
+                              c->opt.slab > 0 ? c->opt.slab : (ncls_s > 1 ? 8 : 0), c->opt.form, ncls_s, 1);
     const size_t order_bytes = tensor ? tile_order_bytes(pl) : 0;
     const size_t nn = (size_t)n;
     // the problem's workspace, then the two bandwidth record arrays
@@ -775,8 +778,7 @@ stkde_status stkde_compute_batch(stkde_ctx* c, const stkde_problem* probs, int c
         if (pkinds[i] == 0 && cap) return STKDE_ERR_UNSUPPORTED;  // host events in a graph
         ProblemDev& P = tab[i];
         P = ProblemDev{};
-        P.pl = make_plan(c->opt.kernel_constants, q.n, &q.grid, q.hs, q.ht, c->opt.slab,
-                         form == STKDE_FORM_FP32);
+        P.pl = make_plan(c->opt.kernel_constants, q.n, &q.grid, q.hs, q.ht, c->opt.slab, form);
         P.x0 = q.grid.x0; P.y0 = q.grid.y0; P.t0 = q.grid.t0;
         P.sres = q.grid.sres; P.tres = q.grid.tres;
         P.isres = 1.0 / q.grid.sres; P.itres = 1.0 / q.grid.tres;
@@ -882,8 +884,7 @@ static stkde_status count_updates(stkde_ctx* c, const double* points, int64_t n,
     if (capturing(c)) return STKDE_ERR_UNSUPPORTED;  // synchronous
     const int pkind = pointer_kind(points, c->device);
     if (pkind < 0) return STKDE_ERR_INVALID_ARGUMENT;
-    const Plan pl = make_plan(c->opt.kernel_constants, n, g, hs, ht, c->opt.slab,
-                              c->opt.form == STKDE_FORM_FP32);
+    const Plan pl = make_plan(c->opt.kernel_constants, n, g, hs, ht, c->opt.slab, c->opt.form);
     Workspace w;
     const size_t nn = (size_t)n;
     const size_t base = carve(nullptr, (int)n, pl.nkeys, pkind == 0, 0, nullptr);
