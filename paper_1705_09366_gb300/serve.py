@@ -157,6 +157,7 @@ class Server:
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
         self.ctxs = [pkg.Context(device=device, stream=s, form=form) for s in self.streams]
         self.cancelled: set = set()
+        self.inflight_bytes = 0  # bytes of the batches on the device now (run() keeps it)
 
     def set_bytes(self, set_id: int) -> int:
         return self.WORKSPACE_BYTES_PER_EVENT * int(self.sets[set_id].shape[0])
@@ -243,6 +244,7 @@ class Server:
                         if keep_outputs(r):
                             kept[r.rid] = o
                     inflight[s] = None
+            self.inflight_bytes = sum(f[4] for f in inflight if f is not None)
             # admit into free slots while memory allows
             launched = False
             for s in range(len(inflight)):
@@ -259,6 +261,7 @@ class Server:
                 max_admitted = max(max_admitted, busy + nbytes)
                 outs, begin, end = self._launch(s, batch)
                 inflight[s] = (batch, outs, begin, end, nbytes)
+                self.inflight_bytes = busy + nbytes
                 intervals_ev.append((begin, end))
                 batches.append([r.rid for r in batch])
                 launched = True

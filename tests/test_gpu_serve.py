@@ -113,3 +113,21 @@ def test_cancelled_and_expired_requests_are_dropped(sets):
         assert all(3 not in b and 4 not in b for b in batches)
     finally:
         srv.close()
+
+
+def test_admission_follows_free_device_memory(sets):
+    """Device memory that batches in flight use up (600 MB above the reserve in
+    all, as cudaMemGetInfo would report it without a caching allocator): the
+    bytes in flight never exceed 600 MB, whatever the cap; every request is
+    still served, several batches at a time."""
+    srv = serve.Server(sets, budget_bytes=8 << 30, slots=3, reserve_bytes=1 << 30)
+    try:
+        srv.run([_req(0, 0, 128, 128, 5.0, 4.0, 0.0)])  # warm-up
+        srv.free_bytes = lambda: srv.reserve + (600 << 20) - srv.inflight_bytes
+        reqs = [_req(i, i % 3, 256, 256, 10.0, 8.0, 0.0) for i in range(12)]  # a burst
+        stats, lat, batches, _ = srv.run(reqs)
+        assert sorted(lat) == list(range(12))
+        assert 0 < stats["max_admitted_bytes"] <= 600 << 20, stats["max_admitted_bytes"]
+        assert len(batches) > 1
+    finally:
+        srv.close()
