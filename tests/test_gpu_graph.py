@@ -128,3 +128,42 @@ def test_capture_refuses_host_events_in_a_batch():
             assert e.value.status == pkg.ERR_UNSUPPORTED
         g.replay()
         torch.cuda.synchronize()
+
+
+def test_reserve_lets_a_larger_problem_be_captured():
+    """stkde_reserve grows the workspace up front: after a warm-up on a small
+    problem, a larger one (whose workspace would otherwise have to grow, which a
+    capture refuses) is captured and replayed to the direct call's bits, and the
+    call allocates no device memory."""
+    small, big = synth.small(), synth.medium()
+    s = torch.cuda.Stream()
+    with pkg.Context(stream=s) as c:
+        c.compute(torch.from_numpy(small.points).cuda(), (small.gx, small.gy, small.gt),
+                  small.hs, small.ht, out=torch.empty((small.gx, small.gy, small.gt),
+                                                      dtype=torch.float32, device="cuda"))
+        c.synchronize()
+        pts = torch.from_numpy(big.points).cuda()
+        dims = (big.gx, big.gy, big.gt)
+        out = torch.empty(dims, dtype=torch.float32, device="cuda")
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            out.zero_()
+            with pytest.raises(pkg.StkdeError) as e:  # the workspace would have to grow
+                c.compute(pts, dims, big.hs, big.ht, out=out)
+            assert e.value.status == pkg.ERR_UNSUPPORTED
+        c.reserve(64 << 20)  # 56 B per event and 4 B per 512 voxels fit in 64 MB
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        c.compute(pts, dims, big.hs, big.ht, out=out)  # a direct call allocates nothing now
+        c.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            c.compute(pts, dims, big.hs, big.ht, out=out)
+        out.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        replayed = out.clone()
+        c.compute(pts, dims, big.hs, big.ht, out=out)
+        c.synchronize()
+        assert torch.equal(replayed, out)
