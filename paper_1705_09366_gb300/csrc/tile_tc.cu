@@ -1007,18 +1007,20 @@ k_tile_tc(ProblemDev single, const ProblemDev* __restrict__ table, int nprob,
                 if (!first && !hit) continue;
                 uint32_t r[32];
                 const uint32_t ta = trow + (uint32_t)(p * NB + col);
+                const int nv = min(32, nbv - col);
+                float4* p4 = reinterpret_cast<float4*>(dst + col);
+                float4 pv[8];
+                // earlier drains of this block: their sums are read back while the
+                // tensor-memory load is in flight
+                if (valid && vec && nv == 32 && !first) {
+#pragma unroll
+                    for (int v4 = 0; v4 < 8; ++v4) pv[v4] = p4[v4];
+                }
                 ptx::tmem_ld32(ta, r);
                 ptx::tmem_wait_ld();
                 if (hit) ptx::tmem_st32_zero(ta);
                 if (!valid) continue;
-                const int nv = min(32, nbv - col);
                 if (vec && nv == 32) {
-                    float4* p4 = reinterpret_cast<float4*>(dst + col);
-                    float4 pv[8];
-                    if (!first) {  // earlier drains of this block: load all, then add
-#pragma unroll
-                        for (int v4 = 0; v4 < 8; ++v4) pv[v4] = p4[v4];
-                    }
 #pragma unroll
                     for (int v4 = 0; v4 < 8; ++v4) {
                         float4 o = make_float4(__uint_as_float(r[4 * v4]) * scale,
