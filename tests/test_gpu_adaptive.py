@@ -166,8 +166,9 @@ def test_invalid_bandwidths_and_forms(case):
         assert call(ctx, None, None, 0) == pkg.OK
         ctx.synchronize()
         assert not out.any().item()
-    with pkg.Context(form="scatter") as ctx:
-        assert call(ctx, c["hs"], c["ht"]) == pkg.ERR_UNSUPPORTED
+    for form in ("scatter", "tf32x3", "tf32x1"):  # fixed bandwidths only
+        with pkg.Context(form=form) as ctx:
+            assert call(ctx, c["hs"], c["ht"]) == pkg.ERR_UNSUPPORTED
     with pkg.Context(form="fp16x3") as ctx:
         wide = c["hs"].copy()
         wide[0] = wide.max() * 200.0

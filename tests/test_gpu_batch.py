@@ -24,7 +24,7 @@ from paper_1705_09366_gb300 import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-FORMS = ["bf16x3", "fp16x3", "fp32"]
+FORMS = ["bf16x3", "fp16x3", "tf32x3", "tf32x1", "fp32"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -92,8 +92,9 @@ def test_batch_bitwise_equals_single_calls(form, workloads):
             assert torch.equal(g, ref), w.name
 
 
-def test_batch_against_oracle(workloads):
-    with pkg.Context(form="bf16x3") as c:
+@pytest.mark.parametrize("form", ["bf16x3", "tf32x3", "fp32"])
+def test_batch_against_oracle(form, workloads):
+    with pkg.Context(form=form) as c:
         got = _batch(c, workloads)
     for k, (w, g) in enumerate(zip(workloads, got)):
         p = oracle.params(w.gx, w.gy, w.gt, w.hs, w.ht, x0=w.x0, y0=w.y0, t0=w.t0, sres=w.sres,
@@ -111,7 +112,7 @@ def test_batch_against_oracle(workloads):
                 err = max(err, pu.excess_error(sub, ref, slack, scale=scale))
         if w.n == 0:
             assert not g.any().item()
-        assert err <= pu.TOL["bf16x3"], (w.name, err)
+        assert err <= pu.TOL[form], (w.name, err)
 
 
 def test_batch_invalid_arguments(workloads):
