@@ -22,6 +22,7 @@ takes them from stkde_abramson_bandwidths (a pilot density by Abramson's law).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -685,8 +686,15 @@ def run_batch(pkg, torch, form, count):
         c.synchronize()
         direct = [o.clone() for o in outs]
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=stream):
-            c.compute_batch(probs)
+        # no garbage collection inside the capture: destroying stray CUDA objects
+        # there would invalidate a global-mode capture
+        gc.collect()
+        gc.disable()
+        try:
+            with torch.cuda.graph(g, stream=stream):
+                c.compute_batch(probs)
+        finally:
+            gc.enable()
         with torch.cuda.stream(stream):  # replays run on torch's current stream
             for o in outs:
                 o.fill_(float("nan"))

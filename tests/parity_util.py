@@ -1,6 +1,9 @@
 """Helpers shared by the GPU parity tests (no STKDE arithmetic here)."""
 from __future__ import annotations
 
+import contextlib
+import gc
+
 import numpy as np
 
 # Gates from the accuracy targets: max |gpu - oracle| / max(oracle), after the
@@ -49,3 +52,21 @@ def sample_tile_boxes(points, gx, gy, gt, n_random=48, seed=0, cell=(16, 8)):
         boxes.append((cx * cell[0], min(gx, (cx + 1) * cell[0]), cy * cell[1],
                       min(gy, (cy + 1) * cell[1]), 0, gt))
     return boxes
+
+
+@contextlib.contextmanager
+def captured(torch, graph, stream, **kw):
+    """torch.cuda.graph with Python's garbage collector held off.  A collection
+    inside the capture could destroy CUDA objects left by earlier tests (events,
+    graphs, streams); an ongoing global-mode capture forbids those calls and
+    would be invalidated for reasons outside the code under test."""
+    gc.collect()
+    torch.cuda.synchronize()
+    was = gc.isenabled()
+    gc.disable()
+    try:
+        with torch.cuda.graph(graph, stream=stream, **kw):
+            yield
+    finally:
+        if was:
+            gc.enable()

@@ -19,6 +19,7 @@ import numpy as np
 import pytest
 
 import paper_1705_09366_gb300 as pkg
+import parity_util as pu
 from paper_1705_09366_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -160,7 +161,7 @@ def test_capture_refuses_growth_and_keeps_the_capture_valid():
     s = torch.cuda.Stream()
     with pkg.Context(stream=s) as c:  # fresh: empty workspace
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
+        with pu.captured(torch, g, s):
             out.zero_()
             with pytest.raises(pkg.StkdeError) as e:
                 c.compute(pts, (w.gx, w.gy, w.gt), w.hs, w.ht, out=out)

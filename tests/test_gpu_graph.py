@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import paper_1705_09366_gb300 as pkg
+import parity_util as pu
 from paper_1705_09366_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -40,7 +41,7 @@ def test_graph_replay_matches_direct_calls(form):
         c.synchronize()
         ref1 = out.clone()
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
+        with pu.captured(torch, g, s):
             pkg.stkde_compute(c.handle, pts, w.n, grid, w.hs, w.ht, out)
         out.zero_()
         g.replay()
@@ -90,7 +91,7 @@ def test_graph_replay_of_a_batch(form):
             c.synchronize()
             assert torch.equal(alone, r)
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
+        with pu.captured(torch, g, s):
             c.compute_batch(probs)
         for o in outs:
             o.fill_(float("nan"))
@@ -121,7 +122,7 @@ def test_capture_refuses_host_events_in_a_batch():
         c.compute_batch([(dpts, (w.gx, w.gy, w.gt), w.hs, w.ht, out)])
         c.synchronize()
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
+        with pu.captured(torch, g, s):
             out.zero_()
             with pytest.raises(pkg.StkdeError) as e:
                 c.compute_batch([(w.points, (w.gx, w.gy, w.gt), w.hs, w.ht, out)])
@@ -146,7 +147,7 @@ def test_reserve_lets_a_larger_problem_be_captured():
         dims = (big.gx, big.gy, big.gt)
         out = torch.empty(dims, dtype=torch.float32, device="cuda")
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
+        with pu.captured(torch, g, s):
             out.zero_()
             with pytest.raises(pkg.StkdeError) as e:  # the workspace would have to grow
                 c.compute(pts, dims, big.hs, big.ht, out=out)
@@ -158,7 +159,7 @@ def test_reserve_lets_a_larger_problem_be_captured():
         c.synchronize()
         assert torch.cuda.mem_get_info()[0] == free0
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
+        with pu.captured(torch, g, s):
             c.compute(pts, dims, big.hs, big.ht, out=out)
         out.fill_(float("nan"))
         g.replay()

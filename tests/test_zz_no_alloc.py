@@ -41,8 +41,8 @@ def _allocating(form, w, pts):
 
 
 @pytest.mark.parametrize("wname,form", [("small", "bf16x3"), ("small", "fp32"),
-                                        ("small", "fp16x3"), ("small", "scatter"),
-                                        ("medium", "bf16x3")])
+                                        ("small", "fp16x3"), ("small", "tf32x3"),
+                                        ("small", "scatter"), ("medium", "bf16x3")])
 def test_static_entry_matches_allocating_entry_twice(wname, form):
     w = synth.WORKLOADS[wname]()
     pts = torch.from_numpy(w.points).cuda()
@@ -74,7 +74,7 @@ def test_static_entry_allocates_nothing():
     # captured in global mode (any cudaMalloc in the call would invalidate the capture)
     s = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=s, capture_error_mode="global"):
+    with pu.captured(torch, g, s, capture_error_mode="global"):
         pkg.stkde_compute_static(pts, w.n, grid, w.hs, w.ht, out, stream=s, sync=False)
     out.fill_(float("nan"))
     g.replay()
@@ -82,7 +82,7 @@ def test_static_entry_allocates_nothing():
     assert torch.equal(out, ref)
     # a captured call cannot wait for its stream
     g2 = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g2, stream=s, capture_error_mode="global"):
+    with pu.captured(torch, g2, s, capture_error_mode="global"):
         out.zero_()
         with pytest.raises(pkg.StkdeError) as e:
             pkg.stkde_compute_static(pts, w.n, grid, w.hs, w.ht, out, stream=s, sync=True)
